@@ -1,0 +1,101 @@
+/*
+ * wz.h - C ABI of the GB300 lattice Wess-Zumino fermion-matrix library.
+ *
+ * The library applies the fermion matrix of the lattice Wess-Zumino model with
+ * Ginsparg-Wilson (overlap) fermions (Chen, Dzienkowski, Giedt):
+ *
+ *   M = Dslash + (m + c g phi) P_+ + (m^* + c g^* phi^*) P_-,
+ *   Dslash = (1 - a D2/2)^-1 D1                                   (Eq. fmat)
+ *
+ * through a 4D lattice FFT (the "FFT trick" of Sec. 7.2), and uses it in
+ * conjugate-gradient solves of M^dagger M x = b (Eq. theprob), optionally
+ * preconditioned by the free operator M0^-1 (Sec. 7.3), in the pseudofermion
+ * force and in hybrid Monte Carlo trajectories (Sec. 7.2).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - a = 1.  dims = {T, Z, Y, X}; T even (antiperiodic fermion time, Sec. 3.1);
+ *   X == Y; every extent in the supported set returned by wz_supported_extent.
+ * - Spinor field: complex, interleaved (re, im), layout [nrhs][T][Z][Y][X][4],
+ *   spin index fastest.  WZ_C64 = complex64 (2 x float), WZ_C128 = complex128.
+ * - Scalar field phi: complex128 [T][Z][Y][X], periodic in every direction.
+ * - Force / gradient: complex128 [T][Z][Y][X] holding (dS/dphi_R, dS/dphi_I).
+ * - Chiral basis of Sec. 2.1: gamma_5 = diag(-1,-1,1,1), P_- = spins 0,1,
+ *   P_+ = spins 2,3; direction mu = 0 is time, mu = 1, 2, 3 are x, y, z.
+ * - Fourier convention f(p) = sum_x exp(-i p.x) f(x); p_t = pi (2n+1)/T.
+ *
+ * Ownership: all field pointers belong to the caller.  Device pointers are used
+ * in place, asynchronously on the context stream.  Host pointers (pageable or
+ * pinned) are accepted by wz_set_phi, wz_apply, wz_solve, wz_force and
+ * wz_action: the call stages them through context-owned device buffers and
+ * returns after the results are back in host memory.  The context owns its
+ * tables, workspace and RNG state; it is not thread-safe.
+ *
+ * Errors: every call returns a WZ_* status; nothing throws across the ABI.
+ * wz_last_error returns a message for the most recent failure of that context.
+ */
+#ifndef WZ_H
+#define WZ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum wz_status {
+  WZ_OK = 0,
+  WZ_EINVAL = 1,          /* bad argument: null pointer, odd T, unsupported extent, ... */
+  WZ_ENOMEM = 2,          /* device allocation failed */
+  WZ_ECUDA = 3,           /* CUDA runtime error (message in wz_last_error) */
+  WZ_NOT_CONVERGED = 4,   /* solver hit maxiter; x holds the best iterate, stats filled */
+  WZ_EUNSUPPORTED = 5     /* combination not built (e.g. an extent without kernels) */
+};
+
+enum wz_dtype { WZ_C64 = 0, WZ_C128 = 1 };
+
+enum wz_op {
+  WZ_OP_M = 0,            /* M psi                                     (Eq. fmat) */
+  WZ_OP_MDAG = 1,         /* M^dagger psi = -Dslash psi + Y^dagger psi             */
+  WZ_OP_MDAGM = 2,        /* (M^dagger M + shift) psi                  (Eq. yuier) */
+  WZ_OP_DSLASH = 3,       /* Dslash psi                        (Sec. 3.2 probe) */
+  WZ_OP_M0INV = 4,        /* M0^-1 psi, M0^-1 = M0^dagger/(D^dagger D + |m|^2) (Sec. 7.3) */
+  WZ_OP_M0INV_DAG = 5,    /* (M0^-1)^dagger psi                                   */
+  WZ_OP_MTILDE = 6,       /* M~ psi = M M0^-1 psi                   (Eq. theprob) */
+  WZ_OP_MTILDE_DAG = 7,   /* M~^dagger psi                                        */
+  WZ_OP_MTILDE_DAGM = 8   /* (M~^dagger M~ + shift) psi                           */
+};
+
+/* Lattice and action parameters (Sec. 2.2, Eq. fmat, Eq. acws). */
+typedef struct wz_params {
+  int dims[4];            /* T, Z, Y, X */
+  double m_re, m_im;      /* bare mass m */
+  double g_re, g_im;      /* Yukawa coupling g */
+  double r;               /* Wilson parameter (paper: 1) */
+  double M0;              /* constant of the kernel A = M0 - D_W (paper: 1) */
+  double yukawa;          /* c in c g phi P_+ : 2 in Eq. fmat, 1 in Sec. 7.1 */
+} wz_params;
+
+typedef struct wz_ctx wz_ctx;
+
+/* Create a context on the current CUDA device.  stream is a cudaStream_t
+ * (NULL = legacy default stream).  Computes the momentum-space tables
+ * h(p) = 2/(omega+b) etc. in FP64 on the device (Sec. 3.1, Eq. d1mom).
+ * Returns WZ_EINVAL for odd T, X != Y or an extent without kernels. */
+int wz_create(const wz_params* p, void* stream, wz_ctx** out);
+int wz_destroy(wz_ctx* ctx);
+const char* wz_last_error(const wz_ctx* ctx);
+/* 1 if an extent n has compiled kernels (spatial / time), else 0. */
+int wz_supported_extent(int n);
+
+/* Set the scalar field phi (complex128 [T][Z][Y][X], host or device).  The
+ * context keeps an FP64 copy and an FP32 copy for the inner solver. */
+int wz_set_phi(wz_ctx* ctx, const void* phi);
+
+/* out = op(in) for nrhs fields of the given dtype (wz_op).  shift is added
+ * for the *_DAGM ops.  in and out may alias.  Asynchronous for device
+ * pointers. */
+int wz_apply(wz_ctx* ctx, int op, int dtype, const void* in, void* out, int nrhs, double shift);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* WZ_H */

@@ -1,0 +1,169 @@
+"""ctypes binding of the C ABI declared in include/wz.h (argument marshalling only).
+
+Every function here forwards to the entry point of the same name in libwz.so;
+all arithmetic runs in the library's CUDA kernels.  Fields may be torch
+tensors (device or host) or numpy arrays (host); both must be C-contiguous
+with dtype complex64 (WZ_C64) or complex128 (WZ_C128).  There is no fallback:
+if libwz.so is missing or fails to load, importing this module raises.
+"""
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(HERE, "libwz.so")
+
+WZ_OK, WZ_EINVAL, WZ_ENOMEM, WZ_ECUDA, WZ_NOT_CONVERGED, WZ_EUNSUPPORTED = range(6)
+WZ_C64, WZ_C128 = 0, 1
+(WZ_OP_M, WZ_OP_MDAG, WZ_OP_MDAGM, WZ_OP_DSLASH, WZ_OP_M0INV, WZ_OP_M0INV_DAG,
+ WZ_OP_MTILDE, WZ_OP_MTILDE_DAG, WZ_OP_MTILDE_DAGM) = range(9)
+OPS = {"M": WZ_OP_M, "Mdag": WZ_OP_MDAG, "MdagM": WZ_OP_MDAGM, "Dslash": WZ_OP_DSLASH,
+       "M0inv": WZ_OP_M0INV, "M0inv_dag": WZ_OP_M0INV_DAG, "Mtilde": WZ_OP_MTILDE,
+       "Mtilde_dag": WZ_OP_MTILDE_DAG, "Mtilde_dagM": WZ_OP_MTILDE_DAGM}
+
+
+class WzParams(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int * 4), ("m_re", ctypes.c_double), ("m_im", ctypes.c_double),
+                ("g_re", ctypes.c_double), ("g_im", ctypes.c_double), ("r", ctypes.c_double),
+                ("M0", ctypes.c_double), ("yukawa", ctypes.c_double)]
+
+
+class WzError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"wz status {code}: {msg}")
+        self.code = code
+
+
+def _load():
+    if not os.path.exists(LIBPATH):
+        raise ImportError(f"{LIBPATH} is missing: run __graft_entry__.build() (nvcc, sm_103a) first")
+    lib = ctypes.CDLL(LIBPATH)
+    P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "wz_create": ([ctypes.POINTER(WzParams), P, ctypes.POINTER(P)], I),
+        "wz_destroy": ([P], I),
+        "wz_last_error": ([P], ctypes.c_char_p),
+        "wz_supported_extent": ([I], I),
+        "wz_set_phi": ([P, P], I),
+        "wz_apply": ([P, I, I, P, P, I, D], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    return lib
+
+
+LIB = _load()
+
+EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply")
+
+
+def _is_torch(x):
+    return type(x).__module__.startswith("torch")
+
+
+def field_ptr(x, dtype=None):
+    """(pointer, wz dtype) of a contiguous complex field (torch tensor or numpy array)."""
+    if _is_torch(x):
+        import torch
+        if not x.is_contiguous():
+            raise ValueError("field must be contiguous")
+        dt = {torch.complex64: WZ_C64, torch.complex128: WZ_C128}.get(x.dtype)
+        ptr = x.data_ptr()
+    else:
+        if not (isinstance(x, np.ndarray) and x.flags["C_CONTIGUOUS"]):
+            raise ValueError("field must be a C-contiguous numpy array or torch tensor")
+        dt = {np.dtype(np.complex64): WZ_C64, np.dtype(np.complex128): WZ_C128}.get(x.dtype)
+        ptr = x.ctypes.data
+    if dt is None:
+        raise ValueError(f"unsupported dtype {x.dtype}")
+    if dtype is not None and dt != dtype:
+        raise ValueError("dtype mismatch")
+    return ctypes.c_void_p(ptr), dt
+
+
+def check(ctx, rc):
+    if rc != WZ_OK:
+        msg = LIB.wz_last_error(ctx).decode() if ctx else ""
+        raise WzError(rc, msg)
+    return rc
+
+
+def make_params(dims, m=0.1, g=0.1, r=1.0, M0=1.0, yukawa=2.0):
+    p = WzParams()
+    for i in range(4):
+        p.dims[i] = int(dims[i])
+    m, g = complex(m), complex(g)
+    p.m_re, p.m_im, p.g_re, p.g_im = m.real, m.imag, g.real, g.imag
+    p.r, p.M0, p.yukawa = float(r), float(M0), float(yukawa)
+    return p
+
+
+def wz_create(params, stream=None):
+    h = ctypes.c_void_p()
+    check(None, LIB.wz_create(ctypes.byref(params), ctypes.c_void_p(stream or 0), ctypes.byref(h)))
+    return h
+
+
+def wz_destroy(ctx):
+    return LIB.wz_destroy(ctx)
+
+
+def wz_last_error(ctx):
+    return LIB.wz_last_error(ctx).decode()
+
+
+def wz_supported_extent(n):
+    return bool(LIB.wz_supported_extent(int(n)))
+
+
+def wz_set_phi(ctx, phi):
+    ptr, dt = field_ptr(phi)
+    if dt != WZ_C128:
+        raise ValueError("phi must be complex128")
+    return check(ctx, LIB.wz_set_phi(ctx, ptr))
+
+
+def wz_apply(ctx, op, inp, out, nrhs, shift=0.0):
+    pin, dt = field_ptr(inp)
+    pout, _ = field_ptr(out, dt)
+    op = OPS.get(op, op)
+    return check(ctx, LIB.wz_apply(ctx, int(op), dt, pin, pout, int(nrhs), float(shift)))
+
+
+class Lattice:
+    """Owns one wz_ctx; methods forward to the C entry points of the same name."""
+
+    def __init__(self, dims, m=0.1, g=0.1, r=1.0, M0=1.0, yukawa=2.0, stream=None):
+        self.dims = tuple(int(d) for d in dims)
+        self.params = make_params(dims, m, g, r, M0, yukawa)
+        if stream is None:
+            try:
+                import torch
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        self.ctx = wz_create(self.params, stream)
+
+    def close(self):
+        if self.ctx:
+            wz_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_phi(self, phi):
+        return wz_set_phi(self.ctx, phi)
+
+    def apply(self, op, inp, out, nrhs=None, shift=0.0):
+        if nrhs is None:
+            nrhs = inp.numel() // (4 * int(np.prod(self.dims))) if _is_torch(inp) else inp.size // (4 * int(np.prod(self.dims)))
+        return wz_apply(self.ctx, op, inp, out, nrhs, shift)

@@ -1,0 +1,281 @@
+// C ABI entry points: context, tables, phi, apply.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "apply_impl.cuh"
+#include "wz_ctx.h"
+
+namespace wz {
+
+int set_error(wz_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  return code;
+}
+
+int cuda_error(wz_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string("CUDA error ") + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ") at " + where;
+  return set_error(c, e == cudaErrorMemoryAllocation ? WZ_ENOMEM : WZ_ECUDA, m);
+}
+
+bool is_device_pointer(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+bool extent_supported(int n) {
+  switch (n) {
+#define WZ_CASE(k) \
+  case k: return true;
+    WZ_FOR_EXTENTS(WZ_CASE)
+#undef WZ_CASE
+  }
+  return false;
+}
+
+bool zt_supported(int nz, int nt) {
+#define WZ_CASE(z, t) \
+  if (nz == z && nt == t) return true;
+  WZ_FOR_ZT_PAIRS(WZ_CASE)
+#undef WZ_CASE
+  return false;
+}
+
+// ----------------------------------------------------------------------------- tables (a0)
+// One thread per fermion momentum p = (pi(2nt+1)/T, 2pi nz/Z, 2pi ny/Y, 2pi nx/X):
+//   b = M0 - r sum_mu 2 sin^2(p_mu/2),  omega = sqrt(b^2 + sum sin^2 p_mu),
+//   h = 2/(omega + b),  den = h^2 sum sin^2 p_mu + |m|^2              (Sec. 3.1, 7.3)
+// Evaluated in FP64; the FP32 table is the rounded FP64 value.
+struct TableArgs {
+  int T, Z, Y, X;
+  double r, M0, m2, invV;
+  double *hV, *hdV, *dV;
+  float *hVf, *hdVf, *dVf;
+};
+
+__global__ void momentum_tables_kernel(TableArgs a) {
+  const long V = (long)a.T * a.Z * a.Y * a.X;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
+    const int nx = (int)(i % a.X);
+    const int ny = (int)((i / a.X) % a.Y);
+    const int nz = (int)((i / ((long)a.X * a.Y)) % a.Z);
+    const int nt = (int)(i / ((long)a.X * a.Y * a.Z));
+    // angles in units of pi
+    const double ang[4] = {(2.0 * nt + 1.0) / a.T, 2.0 * nz / a.Z, 2.0 * ny / a.Y, 2.0 * nx / a.X};
+    double s2 = 0.0, w = 0.0;
+    for (int mu = 0; mu < 4; ++mu) {
+      double sn, cs;
+      sincospi(ang[mu], &sn, &cs);
+      s2 += sn * sn;
+      w += 1.0 - cs;  // 2 sin^2(p/2)
+    }
+    const double b = a.M0 - a.r * w;
+    const double omega = sqrt(b * b + s2);
+    const double h = 2.0 / (omega + b);
+    const double den = h * h * s2 + a.m2;
+    a.hV[i] = h * a.invV;
+    a.hdV[i] = h / den * a.invV;
+    a.dV[i] = a.invV / den;
+    a.hVf[i] = (float)a.hV[i];
+    a.hdVf[i] = (float)a.hdV[i];
+    a.dVf[i] = (float)a.dV[i];
+  }
+}
+
+// per-axis tables: [sinT(T) sinZ(Z) sinY(Y) sinX(X) twc(T) tws(T)]
+__global__ void axis_tables_kernel(int T, int Z, int Y, int X, double* d, float* f) {
+  const int n = 3 * T + Z + Y + X;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v;
+    if (i < T) {
+      v = sinpi((2.0 * i + 1.0) / T);
+    } else if (i < T + Z) {
+      v = sinpi(2.0 * (i - T) / Z);
+    } else if (i < T + Z + Y) {
+      v = sinpi(2.0 * (i - T - Z) / Y);
+    } else if (i < T + Z + Y + X) {
+      v = sinpi(2.0 * (i - T - Z - Y) / X);
+    } else if (i < 2 * T + Z + Y + X) {
+      v = cospi((double)(i - (T + Z + Y + X)) / T);
+    } else {
+      v = sinpi((double)(i - (2 * T + Z + Y + X)) / T);
+    }
+    d[i] = v;
+    f[i] = (float)v;
+  }
+}
+
+template <typename R> static void carve(Tables<R>& t, R* base, long V, int T, int Z, int Y, int X) {
+  t.hV = base;
+  t.hdV = base + V;
+  t.dV = base + 2 * V;
+  R* ax = base + 3 * V;
+  t.sinT = ax;
+  t.sinZ = ax + T;
+  t.sinY = ax + T + Z;
+  t.sinX = ax + T + Z + Y;
+  t.twc = ax + T + Z + Y + X;
+  t.tws = ax + 2 * T + Z + Y + X;
+}
+
+static int build_tables(wz_ctx* c) {
+  const long V = c->V;
+  const long naxis = 3L * c->T + c->Z + c->Y + c->X;
+  const long n = 3 * V + naxis;
+  WZ_CUDA_TRY(c, cudaMalloc(&c->t64.block, n * sizeof(double)));
+  WZ_CUDA_TRY(c, cudaMalloc(&c->t32.block, n * sizeof(float)));
+  carve(c->t64, (double*)c->t64.block, V, c->T, c->Z, c->Y, c->X);
+  carve(c->t32, (float*)c->t32.block, V, c->T, c->Z, c->Y, c->X);
+  TableArgs a;
+  a.T = c->T;
+  a.Z = c->Z;
+  a.Y = c->Y;
+  a.X = c->X;
+  a.r = c->p.r;
+  a.M0 = c->p.M0;
+  a.m2 = c->p.m_re * c->p.m_re + c->p.m_im * c->p.m_im;
+  a.invV = 1.0 / (double)V;
+  a.hV = c->t64.hV;
+  a.hdV = c->t64.hdV;
+  a.dV = c->t64.dV;
+  a.hVf = c->t32.hV;
+  a.hdVf = c->t32.hdV;
+  a.dVf = c->t32.dV;
+  const int blocks = (int)((V + 255) / 256 < 1024 ? (V + 255) / 256 : 1024);
+  momentum_tables_kernel<<<blocks, 256, 0, c->stream>>>(a);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  axis_tables_kernel<<<1, 256, 0, c->stream>>>(c->T, c->Z, c->Y, c->X, c->t64.sinT, c->t32.sinT);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  return WZ_OK;
+}
+
+__global__ void phi_to_f32_kernel(const cplx<double>* in, cplx<float>* out, long n) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    out[i] = cplx<float>{(float)in[i].x, (float)in[i].y};
+}
+
+// Stage nbytes of a host or device source into a device pointer usable by kernels.
+static int stage_in(wz_ctx* c, const void* src, size_t nbytes, void* dev_dst) {
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(dev_dst, src, nbytes, cudaMemcpyDefault, c->stream));
+  return WZ_OK;
+}
+
+template <typename R>
+static int apply_typed(wz_ctx* c, int op, const void* in, void* out, int nrhs, double shift) {
+  const size_t field = sizeof(cplx<R>) * 4 * (size_t)c->V * nrhs;
+  WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<R>(c, op, nrhs)));
+  const bool din = is_device_pointer(in), dout = is_device_pointer(out);
+  const cplx<R>* pin = (const cplx<R>*)in;
+  cplx<R>* pout = (cplx<R>*)out;
+  if (!din || !dout) {
+    WZ_CUDA_TRY(c, c->ws_stage.reserve(2 * field));
+    cplx<R>* sin_ = (cplx<R>*)c->ws_stage.ptr;
+    cplx<R>* sout = sin_ + 4 * c->V * nrhs;
+    if (!din) {
+      int rc = stage_in(c, in, field, sin_);
+      if (rc) return rc;
+      pin = sin_;
+    }
+    if (!dout) pout = sout;
+  }
+  int rc = apply_op<R>(c, op, pin, pout, nrhs, (R)shift, (cplx<R>*)c->ws_apply.ptr);
+  if (rc) return rc;
+  if (!dout) {
+    WZ_CUDA_TRY(c, cudaMemcpyAsync(out, pout, field, cudaMemcpyDeviceToHost, c->stream));
+    WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  } else if (!din) {
+    WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));  // host input must stay valid until copied
+  }
+  return WZ_OK;
+}
+
+}  // namespace wz
+
+using namespace wz;
+
+extern "C" {
+
+int wz_supported_extent(int n) { return extent_supported(n) ? 1 : 0; }
+
+int wz_create(const wz_params* p, void* stream, wz_ctx** out) {
+  if (!p || !out) return WZ_EINVAL;
+  *out = nullptr;
+  const int T = p->dims[0], Z = p->dims[1], Y = p->dims[2], X = p->dims[3];
+  if (T <= 0 || Z <= 0 || Y <= 0 || X <= 0 || (T % 2) != 0) return WZ_EINVAL;
+  if (X != Y || !extent_supported(X) || !zt_supported(Z, T)) return WZ_EUNSUPPORTED;
+  if (p->r <= 0.0) return WZ_EINVAL;
+  wz_ctx* c = new (std::nothrow) wz_ctx();
+  if (!c) return WZ_ENOMEM;
+  c->p = *p;
+  c->T = T;
+  c->Z = Z;
+  c->Y = Y;
+  c->X = X;
+  c->V = (long)T * Z * Y * X;
+  c->stream = (cudaStream_t)stream;
+  cudaGetDevice(&c->device);
+  int rc = build_tables(c);
+  if (rc == WZ_OK) {
+    cudaError_t e = cudaMalloc(&c->phi64, sizeof(cplx<double>) * c->V);
+    if (e == cudaSuccess) e = cudaMalloc(&c->phi32, sizeof(cplx<float>) * c->V);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->phi64, 0, sizeof(cplx<double>) * c->V, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->phi32, 0, sizeof(cplx<float>) * c->V, c->stream);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, 1 << 16);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) rc = cuda_error(c, e, "wz_create");
+  }
+  if (rc != WZ_OK) {
+    wz_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return WZ_OK;
+}
+
+int wz_destroy(wz_ctx* c) {
+  if (!c) return WZ_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  if (c->t64.block) cudaFree(c->t64.block);
+  if (c->t32.block) cudaFree(c->t32.block);
+  if (c->phi64) cudaFree(c->phi64);
+  if (c->phi32) cudaFree(c->phi32);
+  if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  c->ws_apply.release();
+  c->ws_stage.release();
+  c->ws_solver.release();
+  c->ws_red.release();
+  c->ws_force.release();
+  delete c;
+  return WZ_OK;
+}
+
+const char* wz_last_error(const wz_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int wz_set_phi(wz_ctx* c, const void* phi) {
+  if (!c || !phi) return set_error(c, WZ_EINVAL, "wz_set_phi: null pointer");
+  const size_t n = sizeof(cplx<double>) * c->V;
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(c->phi64, phi, n, cudaMemcpyDefault, c->stream));
+  phi_to_f32_kernel<<<(unsigned)((c->V + 255) / 256 < 2048 ? (c->V + 255) / 256 : 2048), 256, 0, c->stream>>>(
+      c->phi64, c->phi32, c->V);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  if (!is_device_pointer(phi)) WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->phi_set = true;
+  return WZ_OK;
+}
+
+int wz_apply(wz_ctx* c, int op, int dtype, const void* in, void* out, int nrhs, double shift) {
+  if (!c) return WZ_EINVAL;
+  if (!in || !out || nrhs < 0) return set_error(c, WZ_EINVAL, "wz_apply: bad argument");
+  if (op < WZ_OP_M || op > WZ_OP_MTILDE_DAGM) return set_error(c, WZ_EINVAL, "wz_apply: unknown op");
+  if (nrhs == 0) return WZ_OK;
+  if (dtype == WZ_C128) return apply_typed<double>(c, op, in, out, nrhs, shift);
+  if (dtype == WZ_C64) return apply_typed<float>(c, op, in, out, nrhs, shift);
+  return set_error(c, WZ_EINVAL, "wz_apply: unknown dtype");
+}
+
+}  // extern "C"

@@ -1,0 +1,245 @@
+// Pass sequencing of the operators of wz_op, templated on precision.
+//
+//   M        : xy_fwd(psi) -> zt(+Dslash) -> xy_inv(+ Y psi)
+//   M^dag    : xy_fwd(psi) -> zt(-Dslash) -> xy_inv(+ Y^dag psi)
+//   M^dag M  : xy_fwd(psi) -> zt(+Dslash) -> xy_inv_fwd(C = M psi) -> zt(-Dslash)
+//              -> xy_inv(+ Y^dag C + shift psi)
+//   M~ = 1 + Y_int M0^-1,  M~^dag = 1 + (M0^-1)^dag Y_int^dag   (Sec. 7.3, M0 M0^-1 = 1)
+#pragma once
+#include "wz_ctx.h"
+#include "wz_kernels.cuh"
+
+namespace wz {
+
+// extents with compiled kernels; the xy pass needs X == Y, the zt pass a (Z, T) pair
+#define WZ_FOR_EXTENTS(F) F(4) F(6) F(8) F(12) F(16)
+#define WZ_FOR_ZT_PAIRS(F) F(4, 4) F(6, 6) F(8, 8) F(12, 12) F(16, 16) F(8, 16) F(16, 32) F(8, 32)
+
+template <typename Kern>
+static cudaError_t set_smem(Kern k, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename R, int L, int MODE>
+static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
+  using S = XYShape<L>;
+  const size_t smem = sizeof(cplx<R>) * S::PLANE * S::PPC;
+  static bool attr_done = false;  // one attribute call per instantiation and process
+  if (!attr_done) {
+    cudaError_t e = set_smem(xy_pass<R, L, MODE>, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int grid = (a.nplanes + S::PPC - 1) / S::PPC;
+  if (grid == 0) return cudaSuccess;
+  xy_pass<R, L, MODE><<<grid, S::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int L>
+static cudaError_t launch_xy_L(int mode, const XYArgs<R>& a, cudaStream_t st) {
+  switch (mode) {
+    case XY_FWD: return launch_xy_t<R, L, XY_FWD>(a, st);
+    case XY_FWD_YINTDAG: return launch_xy_t<R, L, XY_FWD_YINTDAG>(a, st);
+    case XY_INV: return launch_xy_t<R, L, XY_INV>(a, st);
+    case XY_INV_Y: return launch_xy_t<R, L, XY_INV_Y>(a, st);
+    case XY_INV_YDAG: return launch_xy_t<R, L, XY_INV_YDAG>(a, st);
+    case XY_INV_Y_FWD: return launch_xy_t<R, L, XY_INV_Y_FWD>(a, st);
+    case XY_INV_PC: return launch_xy_t<R, L, XY_INV_PC>(a, st);
+    case XY_INV_PC_FWD: return launch_xy_t<R, L, XY_INV_PC_FWD>(a, st);
+    case XY_INV_ADD: return launch_xy_t<R, L, XY_INV_ADD>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+static cudaError_t launch_xy(int L, int mode, const XYArgs<R>& a, cudaStream_t st) {
+  switch (L) {
+#define WZ_CASE(n) \
+  case n: return launch_xy_L<R, n>(mode, a, st);
+    WZ_FOR_EXTENTS(WZ_CASE)
+#undef WZ_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, int NZ, int NT, int MUL>
+static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
+  using S = ZTShape<R, NZ, NT>;
+  constexpr int C = S::C;
+  const size_t smem = sizeof(cplx<R>) * NZ * NT * C * 4;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = set_smem(zt_pass<R, NZ, NT, MUL>, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const long grid = (long)nrhs * a.ntiles;
+  if (grid == 0) return cudaSuccess;
+  zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, int NZ, int NT>
+static cudaError_t launch_zt_p(int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
+  switch (mul) {
+    case ZT_DSLASH: return launch_zt_t<R, NZ, NT, ZT_DSLASH>(a, nrhs, st);
+    case ZT_M0INV: return launch_zt_t<R, NZ, NT, ZT_M0INV>(a, nrhs, st);
+    case ZT_M0INV_DAG: return launch_zt_t<R, NZ, NT, ZT_M0INV_DAG>(a, nrhs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R>
+static cudaError_t launch_zt(int nz, int nt, int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
+#define WZ_CASE(z, t) \
+  if (nz == z && nt == t) return launch_zt_p<R, z, t>(mul, a, nrhs, st);
+  WZ_FOR_ZT_PAIRS(WZ_CASE)
+#undef WZ_CASE
+  return cudaErrorInvalidValue;
+}
+
+template <typename R> static SiteCoef<R> site_coef_of(const wz_ctx* c) {
+  SiteCoef<R> k;
+  k.m_re = (R)c->p.m_re;
+  k.m_im = (R)c->p.m_im;
+  k.cg_re = (R)(c->p.yukawa * c->p.g_re);
+  k.cg_im = (R)(c->p.yukawa * c->p.g_im);
+  return k;
+}
+
+template <typename R> static XYArgs<R> xy_args(const wz_ctx* c, int nrhs) {
+  XYArgs<R> a{};
+  a.phi = phi_of<R>(c);
+  a.k = site_coef_of<R>(c);
+  a.nplanes = nrhs * c->T * c->Z;
+  a.TZ = c->T * c->Z;
+  return a;
+}
+
+template <typename R> static int zt_cols(int nz, int nt) {
+  const int n = nz > nt ? nz : nt;
+  return n <= 16 ? ZTTile<R, 16>::C : (n <= 32 ? ZTTile<R, 32>::C : ZTTile<R, 64>::C);
+}
+
+template <typename R> static ZTArgs<R> zt_args(const wz_ctx* c, R sign) {
+  const Tables<R>& t = tables<R>(c);
+  ZTArgs<R> a{};
+  a.hV = t.hV;
+  a.hdV = t.hdV;
+  a.dV = t.dV;
+  a.sinT = t.sinT;
+  a.sinZ = t.sinZ;
+  a.sinY = t.sinY;
+  a.sinX = t.sinX;
+  a.twc = t.twc;
+  a.tws = t.tws;
+  a.sign = sign;
+  a.m_re = (R)c->p.m_re;
+  a.m_im = (R)c->p.m_im;
+  a.X = c->X;
+  a.XY = c->X * c->Y;
+  const int C = zt_cols<R>(c->Z, c->T);
+  a.ntiles = (a.XY + C - 1) / C;
+  return a;
+}
+
+template <typename R> size_t apply_ws_bytes(const wz_ctx* c, int op, int nrhs) {
+  const size_t field = sizeof(cplx<R>) * 4 * (size_t)c->V * nrhs;
+  const bool two = (op == WZ_OP_MDAGM || op == WZ_OP_MTILDE_DAGM);
+  return two ? 2 * field : field;
+}
+
+// ws must hold apply_ws_bytes(c, op, nrhs) bytes.
+template <typename R>
+int apply_op(wz_ctx* c, int op, const cplx<R>* in, cplx<R>* out, int nrhs, R shift, cplx<R>* ws) {
+  const int L = c->X;
+  const long field = 4L * c->V * nrhs;
+  cplx<R>* A = ws;
+  cplx<R>* Cb = ws + field;
+  cudaStream_t st = c->stream;
+  XYArgs<R> xa = xy_args<R>(c, nrhs);
+  cudaError_t e = cudaSuccess;
+#define WZ_RUN(expr)                                    \
+  do {                                                  \
+    e = (expr);                                         \
+    if (e != cudaSuccess) return cuda_error(c, e, #expr); \
+  } while (0)
+
+  auto fwd = [&](int mode, const cplx<R>* src) {
+    XYArgs<R> a = xa;
+    a.psi = src;
+    a.A_out = A;
+    return launch_xy<R>(L, mode, a, st);
+  };
+  auto zt = [&](int mul, R sign) {
+    ZTArgs<R> a = zt_args<R>(c, sign);
+    a.A = A;
+    return launch_zt<R>(c->Z, c->T, mul, a, nrhs, st);
+  };
+  auto inv = [&](int mode, const cplx<R>* psi, const cplx<R>* psi2, cplx<R>* vout, cplx<R>* aout) {
+    XYArgs<R> a = xa;
+    a.A_in = A;
+    a.A_out = aout;
+    a.psi = psi;
+    a.psi2 = psi2;
+    a.shift = shift;
+    a.v_out = vout;
+    return launch_xy<R>(L, mode, a, st);
+  };
+
+  switch (op) {
+    case WZ_OP_M:
+      WZ_RUN(fwd(XY_FWD, in));
+      WZ_RUN(zt(ZT_DSLASH, R(1)));
+      WZ_RUN(inv(XY_INV_Y, in, nullptr, out, nullptr));
+      break;
+    case WZ_OP_MDAG:
+      WZ_RUN(fwd(XY_FWD, in));
+      WZ_RUN(zt(ZT_DSLASH, R(-1)));
+      WZ_RUN(inv(XY_INV_YDAG, in, nullptr, out, nullptr));
+      break;
+    case WZ_OP_MDAGM:
+      WZ_RUN(fwd(XY_FWD, in));
+      WZ_RUN(zt(ZT_DSLASH, R(1)));
+      WZ_RUN(inv(XY_INV_Y_FWD, in, nullptr, Cb, A));
+      WZ_RUN(zt(ZT_DSLASH, R(-1)));
+      WZ_RUN(inv(XY_INV_YDAG, Cb, shift != R(0) ? in : nullptr, out, nullptr));
+      break;
+    case WZ_OP_DSLASH:
+      WZ_RUN(fwd(XY_FWD, in));
+      WZ_RUN(zt(ZT_DSLASH, R(1)));
+      WZ_RUN(inv(XY_INV, nullptr, nullptr, out, nullptr));
+      break;
+    case WZ_OP_M0INV:
+    case WZ_OP_M0INV_DAG:
+      WZ_RUN(fwd(XY_FWD, in));
+      WZ_RUN(zt(op == WZ_OP_M0INV ? ZT_M0INV : ZT_M0INV_DAG, R(1)));
+      WZ_RUN(inv(XY_INV, nullptr, nullptr, out, nullptr));
+      break;
+    case WZ_OP_MTILDE:
+      WZ_RUN(fwd(XY_FWD, in));
+      WZ_RUN(zt(ZT_M0INV, R(1)));
+      WZ_RUN(inv(XY_INV_PC, in, nullptr, out, nullptr));
+      break;
+    case WZ_OP_MTILDE_DAG:
+      WZ_RUN(fwd(XY_FWD_YINTDAG, in));
+      WZ_RUN(zt(ZT_M0INV_DAG, R(1)));
+      WZ_RUN(inv(XY_INV_ADD, in, nullptr, out, nullptr));
+      break;
+    case WZ_OP_MTILDE_DAGM:
+      WZ_RUN(fwd(XY_FWD, in));
+      WZ_RUN(zt(ZT_M0INV, R(1)));
+      WZ_RUN(inv(XY_INV_PC_FWD, in, nullptr, Cb, A));
+      WZ_RUN(zt(ZT_M0INV_DAG, R(1)));
+      WZ_RUN(inv(XY_INV_ADD, Cb, shift != R(0) ? in : nullptr, out, nullptr));
+      break;
+    default:
+      return set_error(c, WZ_EINVAL, "unknown operator");
+  }
+#undef WZ_RUN
+  return WZ_OK;
+}
+
+}  // namespace wz

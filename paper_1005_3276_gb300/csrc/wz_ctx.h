@@ -1,0 +1,101 @@
+// Internal context of the library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+#include "../../include/wz.h"
+#include "wz_fft.cuh"
+
+namespace wz {
+
+// Momentum-space tables of one precision (a0 of the hot path, Sec. 3.1):
+//   hV  = h(p)/V, hdV = h(p)/(den(p) V), dV = 1/(den(p) V),
+//   h = 2/(omega + b), den = h^2 sum sin^2 p + |m|^2  (Sec. 7.3)
+// plus per-axis sin p tables and the antiperiodic twist cos/sin(pi t/T).
+template <typename R> struct Tables {
+  R* hV = nullptr;
+  R* hdV = nullptr;
+  R* dV = nullptr;
+  R* sinT = nullptr;
+  R* sinZ = nullptr;
+  R* sinY = nullptr;
+  R* sinX = nullptr;
+  R* twc = nullptr;
+  R* tws = nullptr;
+  void* block = nullptr;  // single allocation holding everything above
+};
+
+// A device buffer that only grows.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  cudaError_t reserve(size_t n) {
+    if (n <= bytes) return cudaSuccess;
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e == cudaSuccess) bytes = n;
+    return e;
+  }
+  void release() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+  }
+};
+
+}  // namespace wz
+
+struct wz_ctx {
+  wz_params p{};
+  int T = 0, Z = 0, Y = 0, X = 0;
+  long V = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  std::string err;
+
+  wz::Tables<double> t64;
+  wz::Tables<float> t32;
+  wz::cplx<double>* phi64 = nullptr;
+  wz::cplx<float>* phi32 = nullptr;
+  bool phi_set = false;
+
+  wz::DevBuf ws_apply;    // momentum / M psi intermediates of the apply
+  wz::DevBuf ws_stage;    // staging of host buffers
+  wz::DevBuf ws_solver;   // solver vectors
+  wz::DevBuf ws_red;      // reduction partials and per-RHS scalars
+  wz::DevBuf ws_force;    // force / HMC fields
+  void* host_pinned = nullptr;  // small pinned block for scalar read-back
+};
+
+namespace wz {
+
+int set_error(wz_ctx* c, int code, const std::string& msg);
+int cuda_error(wz_ctx* c, cudaError_t e, const char* where);
+bool is_device_pointer(const void* p);
+
+// apply entry (templated on precision), defined in apply_impl.cuh
+template <typename R>
+int apply_op(wz_ctx* c, int op, const cplx<R>* in, cplx<R>* out, int nrhs, R shift, cplx<R>* ws);
+template <typename R> size_t apply_ws_bytes(const wz_ctx* c, int op, int nrhs);
+
+template <typename R> const Tables<R>& tables(const wz_ctx* c);
+template <> inline const Tables<double>& tables<double>(const wz_ctx* c) { return c->t64; }
+template <> inline const Tables<float>& tables<float>(const wz_ctx* c) { return c->t32; }
+template <typename R> const cplx<R>* phi_of(const wz_ctx* c);
+template <> inline const cplx<double>* phi_of<double>(const wz_ctx* c) { return c->phi64; }
+template <> inline const cplx<float>* phi_of<float>(const wz_ctx* c) { return c->phi32; }
+
+bool extent_supported(int n);
+bool zt_supported(int nz, int nt);
+
+}  // namespace wz
+
+#define WZ_CUDA_TRY(c, expr)                                  \
+  do {                                                        \
+    cudaError_t _e = (expr);                                  \
+    if (_e != cudaSuccess) return wz::cuda_error(c, _e, #expr); \
+  } while (0)

@@ -1,0 +1,316 @@
+// Plane-pass kernels of the FFT-based fermion-matrix apply.
+//
+// The Dirac operator of Eq. fmat, Dslash = (1 - D2/2)^-1 D1, is diagonal in
+// momentum space with Dslash(p) = i h(p) gamma_mu sin p_mu, h = 2/(omega + b)
+// (Sec. 3.1, Eq. d1mom).  It is applied as "FFT, multiply, inverse FFT" (the
+// FFT trick of Sec. 7.2).  A 4D FFT of a spinor field [rhs][T][Z][Y][X][4]
+// is split into two plane passes that each keep one whole plane on chip:
+//
+//   xy pass : one (rhs, t, z) plane of Y x X sites, contiguous in memory;
+//             its "phase B" owns y-lines in POSITION space, so every
+//             site-local term (mass, Yukawa, CG vector updates, force
+//             contractions) is fused there.
+//   zt pass : a tile of C consecutive (y, x) columns for all (z, t); forward
+//             FFT over (z, t) with the antiperiodic twist exp(-i pi t/T),
+//             momentum-space spin multiply, inverse FFT, untwist.  In place.
+//
+// M = xy_fwd -> zt(+Dslash) -> xy_inv(+Y psi); M^dagger M fuses the middle xy
+// passes (inverse, + Y psi, store M psi, forward) so it takes five passes.
+//
+// Every thread owns one line (N values of one spin component) in registers
+// and transforms it with wz::fft_line; lines cross between directions through
+// shared memory.  The four spin components of a site sit in four adjacent
+// lanes, so the spin multiply of the zt pass exchanges the opposite-chirality
+// components with warp shuffles.
+#pragma once
+#include "wz_fft.cuh"
+
+namespace wz {
+
+// ----------------------------------------------------------------------------- site terms
+// Y      = (m + c g phi) P_+ + (m^* + c g^* phi^*) P_-       (Eq. fmat)
+// Y_int  =      c g phi  P_+ +        c g^* phi^*  P_-
+// P_- acts on spin components 0, 1 and P_+ on 2, 3 (gamma_5 = diag(-1,-1,1,1)).
+template <typename R> struct SiteCoef {
+  R m_re, m_im;    // bare mass m
+  R cg_re, cg_im;  // c * g with c the Yukawa coefficient (2 in Eq. fmat)
+};
+
+// coefficient multiplying spin component s at a site with field value f
+template <typename R, bool DAG, bool WITH_MASS>
+__device__ __forceinline__ cplx<R> site_coef(const SiteCoef<R>& k, cplx<R> f, int s) {
+  // y_plus = [m] + c g f
+  cplx<R> yp = cplx<R>{k.cg_re, k.cg_im} * f;
+  if (WITH_MASS) yp = yp + cplx<R>{k.m_re, k.m_im};
+  // s >= 2: y_plus ; s < 2: conj(y_plus); dagger conjugates both
+  const bool use_conj = (s < 2) != DAG;
+  return use_conj ? conj(yp) : yp;
+}
+
+// ----------------------------------------------------------------------------- xy pass
+enum XYMode {
+  XY_FWD = 0,          // A_out = F_xy psi
+  XY_FWD_YINTDAG,      // A_out = F_xy (Y_int^dag psi)
+  XY_INV,              // v_out = F_xy^-1 A_in
+  XY_INV_Y,            // v_out = F^-1 A_in + Y psi
+  XY_INV_YDAG,         // v_out = F^-1 A_in + Y^dag psi (+ shift psi2)
+  XY_INV_Y_FWD,        // v = F^-1 A_in + Y psi -> v_out ; A_out = F v
+  XY_INV_PC,           // v_out = psi + Y_int F^-1 A_in
+  XY_INV_PC_FWD,       // v = psi + Y_int F^-1 A_in -> v_out ; A_out = F (Y_int^dag v)
+  XY_INV_ADD,          // v_out = psi + F^-1 A_in (+ shift psi2)
+};
+
+template <int M> struct XYModeInfo {
+  static constexpr bool inv = !(M == XY_FWD || M == XY_FWD_YINTDAG);
+  static constexpr bool fwd = (M == XY_FWD || M == XY_FWD_YINTDAG || M == XY_INV_Y_FWD || M == XY_INV_PC_FWD);
+};
+
+template <typename R> struct XYArgs {
+  const cplx<R>* A_in;   // momentum-space input (inverse passes)
+  cplx<R>* A_out;        // momentum-space output (forward passes)
+  const cplx<R>* psi;    // position-space operand of the site term
+  const cplx<R>* psi2;   // + shift * psi2 (XY_INV_YDAG, XY_INV_ADD), may be null
+  cplx<R>* v_out;        // position-space result of phase B
+  const cplx<R>* phi;    // scalar field [T][Z][Y][X]
+  SiteCoef<R> k;
+  R shift;
+  int nplanes;           // nrhs * T * Z
+  int TZ;                // planes per right-hand side
+};
+
+// Threads per plane: 4 * L (one per (line, spin)); PPC planes per block.
+template <int L> struct XYShape {
+  static constexpr int TPP = 4 * L;
+  static constexpr int PPC = (256 / TPP) > 0 ? (256 / TPP) : 1;
+  static constexpr int THREADS = TPP * PPC;
+  static constexpr int RP = 4 * (L + 1);  // smem row pitch (complex), one site of padding
+  static constexpr int PLANE = L * RP;
+};
+
+template <typename R, int L, int MODE>
+__global__ void __launch_bounds__(XYShape<L>::THREADS)
+xy_pass(XYArgs<R> a) {
+  using S = XYShape<L>;
+  using I = XYModeInfo<MODE>;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
+
+  const int tid = threadIdx.x;
+  const int pl_local = tid / S::TPP;
+  const int w = (tid / 4) % L;  // line coordinate (y in phase A/C, x in phase B)
+  const int s = tid & 3;
+  const long plane = (long)blockIdx.x * S::PPC + pl_local;
+  const bool live = plane < a.nplanes;
+  cplx<R>* P = sm + pl_local * S::PLANE;
+  const long base = plane * (long)(L * L) * 4;  // complex offset of the plane
+
+  cplx<R> v[L];
+
+  // ---------------- phase A: inverse FFT along x of the momentum input
+  if (I::inv) {
+    if (live) {
+#pragma unroll
+      for (int x = 0; x < L; ++x) v[x] = a.A_in[base + (w * L + x) * 4 + s];
+      fft_line<L, +1, R>(v);
+#pragma unroll
+      for (int x = 0; x < L; ++x) P[w * S::RP + x * 4 + s] = v[x];
+    }
+    __syncthreads();
+  }
+
+  // ---------------- phase B: y-line at fixed x = w, spin s, in position space
+  if (live) {
+    const int x = w;
+    const long site0 = plane * (long)(L * L) + x;  // site index of (x, y=0)
+    const long phib = (plane % a.TZ) * (long)(L * L) + x;
+    if (I::inv) {
+#pragma unroll
+      for (int y = 0; y < L; ++y) v[y] = P[y * S::RP + x * 4 + s];
+      fft_line<L, +1, R>(v);
+    }
+#pragma unroll
+    for (int y = 0; y < L; ++y) {
+      const long e = (site0 + y * L) * 4 + s;
+      if constexpr (MODE == XY_FWD) {
+        v[y] = a.psi[e];
+      } else if constexpr (MODE == XY_FWD_YINTDAG) {
+        v[y] = site_coef<R, true, false>(a.k, a.phi[phib + y * L], s) * a.psi[e];
+      } else if constexpr (MODE == XY_INV_Y || MODE == XY_INV_Y_FWD) {
+        v[y] = v[y] + site_coef<R, false, true>(a.k, a.phi[phib + y * L], s) * a.psi[e];
+      } else if constexpr (MODE == XY_INV_YDAG) {
+        v[y] = v[y] + site_coef<R, true, true>(a.k, a.phi[phib + y * L], s) * a.psi[e];
+        if (a.psi2) v[y] = v[y] + a.shift * a.psi2[e];
+      } else if constexpr (MODE == XY_INV_PC || MODE == XY_INV_PC_FWD) {
+        v[y] = a.psi[e] + site_coef<R, false, false>(a.k, a.phi[phib + y * L], s) * v[y];
+      } else if constexpr (MODE == XY_INV_ADD) {
+        v[y] = a.psi[e] + v[y];
+        if (a.psi2) v[y] = v[y] + a.shift * a.psi2[e];
+      }
+      if constexpr (MODE != XY_FWD && MODE != XY_FWD_YINTDAG) {
+        if (a.v_out) a.v_out[e] = v[y];
+      }
+      if constexpr (MODE == XY_INV_PC_FWD) {
+        v[y] = site_coef<R, true, false>(a.k, a.phi[phib + y * L], s) * v[y];
+      }
+    }
+    if (I::fwd) {
+      fft_line<L, -1, R>(v);
+    }
+  }
+  if (!I::fwd) return;
+  // phase B of thread (x, s) rewrites exactly the smem cells it read, so no
+  // barrier is needed between its reads and these writes
+  if (live) {
+#pragma unroll
+    for (int y = 0; y < L; ++y) P[y * S::RP + w * 4 + s] = v[y];
+  }
+  __syncthreads();
+
+  // ---------------- phase C: forward FFT along x, store momentum output
+  if (live) {
+#pragma unroll
+    for (int x = 0; x < L; ++x) v[x] = P[w * S::RP + x * 4 + s];
+    fft_line<L, -1, R>(v);
+#pragma unroll
+    for (int x = 0; x < L; ++x) a.A_out[base + (w * L + x) * 4 + s] = v[x];
+  }
+}
+
+// ----------------------------------------------------------------------------- zt pass
+enum ZTMul {
+  ZT_DSLASH = 0,   // out = sign * i h gamma.sin p  in
+  ZT_M0INV,        // out = (-Dslash + m^* P_+ + m P_-) / den  in
+  ZT_M0INV_DAG,    // out = ( Dslash + m P_+ + m^* P_-) / den  in
+};
+
+template <typename R> struct ZTArgs {
+  cplx<R>* A;          // in/out, momentum in (x, y), position in (z, t)
+  const R* hV;         // h(p) / V
+  const R* hdV;        // h(p) / (den(p) V)
+  const R* dV;         // 1 / (den(p) V)
+  const R* sinT;       // sin p_t  (antiperiodic momenta), length T
+  const R* sinZ;
+  const R* sinY;
+  const R* sinX;
+  const R* twc;        // cos(pi t / T)
+  const R* tws;        // sin(pi t / T)
+  R sign;              // +1 or -1 for ZT_DSLASH
+  R m_re, m_im;
+  int ntiles;          // ceil(XY / C)
+  int X, XY;
+};
+
+// Columns per block: 256 B contiguous per (z, t) row for short lines, fewer
+// columns for long lines so that a block stays at <= 512 threads.
+template <typename R, int NMAX> struct ZTTile {
+  static constexpr int C0 = sizeof(R) == 4 ? 8 : 4;
+  static constexpr int C = NMAX <= 16 ? C0 : (NMAX <= 32 ? C0 / 2 : C0 / 4);
+};
+
+template <typename R, int NZ, int NT> struct ZTShape {
+  static constexpr int NMAX = NZ > NT ? NZ : NT;
+  static constexpr int C = ZTTile<R, NMAX>::C;
+  static constexpr int THREADS = NMAX * C * 4;
+  // every warp must lie entirely inside or outside the t-phase (it shuffles)
+  static_assert((NZ * C * 4) % 32 == 0, "z extent too small for the column tile");
+};
+
+template <typename R, int NZ, int NT, int MUL>
+__global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS)
+zt_pass(ZTArgs<R> a) {
+  constexpr int C = ZTShape<R, NZ, NT>::C;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);  // [t][z][c][s]
+
+  const int tid = threadIdx.x;
+  const int s = tid & 3;
+  const int c = (tid >> 2) % C;
+  const int q = tid / (4 * C);  // t in the z-phase, z in the t-phase
+  const int rhs = blockIdx.x / a.ntiles;
+  const int col_raw = (blockIdx.x % a.ntiles) * C + c;  // (y, x) column = y * X + x
+  // the last tile may be ragged (X * Y not a multiple of C): lanes past the
+  // end keep computing on zeros so that every warp stays whole for the
+  // shuffles, but never touch memory
+  const bool colok = col_raw < a.XY;
+  const int col = colok ? col_raw : 0;
+  const long ZXY = (long)NZ * a.XY;
+  cplx<R>* A = a.A + ((long)rhs * NT * ZXY + col) * 4 + s;
+
+  cplx<R> v[NT > NZ ? NT : NZ];
+
+  // ---------------- z-phase (forward): thread owns (t = q, column, s)
+  if (q < NT) {
+    const int t = q;
+    const cplx<R> tw{a.twc[t], -a.tws[t]};  // exp(-i pi t / T)
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) v[z] = colok ? tw * A[((long)t * ZXY + (long)z * a.XY) * 4] : cplx<R>{R(0), R(0)};
+    fft_ptr<NZ, -1, R>(v);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) sm[((t * NZ + z) * C + c) * 4 + s] = v[z];
+  }
+  __syncthreads();
+
+  // ---------------- t-phase: forward over t, spin multiply, inverse over t
+  if (q < NZ) {
+    const int pz = q;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) v[t] = sm[((t * NZ + pz) * C + c) * 4 + s];
+    fft_ptr<NT, -1, R>(v);
+
+    const int py = col / a.X, px = col - py * a.X;
+    const R sx = a.sinX[px], sy = a.sinY[py], sz = a.sinZ[pz];
+    const int lane = threadIdx.x & 31;
+    const int ulane = (lane & ~3) | (s < 2 ? 2 : 0);  // opposite-chirality pair
+    const R sg = s < 2 ? R(1) : R(-1);
+#pragma unroll
+    for (int pt = 0; pt < NT; ++pt) {
+      const long pidx = ((long)pt * NZ + pz) * a.XY + col;
+      const R st = a.sinT[pt];
+      // row of  sum_mu s_mu gamma_mu  acting on the opposite-chirality pair (u, w)
+      cplx<R> cu, cw;
+      if ((s & 1) == 0) {
+        cu = cplx<R>{st, sg * sz};
+        cw = cplx<R>{sg * sy, sg * sx};
+      } else {
+        cu = cplx<R>{-sg * sy, sg * sx};
+        cw = cplx<R>{st, -sg * sz};
+      }
+      cplx<R> u, ww;
+      u.x = __shfl_sync(0xffffffffu, v[pt].x, ulane);
+      u.y = __shfl_sync(0xffffffffu, v[pt].y, ulane);
+      ww.x = __shfl_sync(0xffffffffu, v[pt].x, ulane + 1);
+      ww.y = __shfl_sync(0xffffffffu, v[pt].y, ulane + 1);
+      const cplx<R> g = cu * u + cw * ww;  // (gamma . sin p  in)_s
+      if constexpr (MUL == ZT_DSLASH) {
+        const R hh = a.sign * a.hV[pidx];
+        v[pt] = hh * mul_i(g);
+      } else {
+        const R hd = a.hdV[pidx], dd = a.dV[pidx];
+        // mass on the diagonal: M0^-1 has m^* on P_+ and m on P_-; the dagger swaps
+        const bool mconj = (MUL == ZT_M0INV) ? (s >= 2) : (s < 2);
+        const cplx<R> mm{a.m_re, mconj ? -a.m_im : a.m_im};
+        const R sd = (MUL == ZT_M0INV) ? R(-1) : R(1);
+        v[pt] = (sd * hd) * mul_i(g) + dd * (mm * v[pt]);
+      }
+    }
+    fft_ptr<NT, +1, R>(v);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) sm[((t * NZ + pz) * C + c) * 4 + s] = v[t];
+  }
+  __syncthreads();
+
+  // ---------------- z-phase (inverse) and untwist exp(+i pi t / T)
+  if (q < NT) {
+    const int t = q;
+    const cplx<R> tw{a.twc[t], a.tws[t]};
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) v[z] = sm[((t * NZ + z) * C + c) * 4 + s];
+    fft_ptr<NZ, +1, R>(v);
+    if (colok) {
+#pragma unroll
+      for (int z = 0; z < NZ; ++z) A[((long)t * ZXY + (long)z * a.XY) * 4] = tw * v[z];
+    }
+  }
+}
+
+}  // namespace wz

@@ -95,6 +95,36 @@ int wz_set_phi(wz_ctx* ctx, const void* phi);
  * pointers. */
 int wz_apply(wz_ctx* ctx, int op, int dtype, const void* in, void* out, int nrhs, double shift);
 
+/* Solver flags (bitwise or). */
+enum wz_solve_flags {
+  WZ_SOLVE_MIXED = 1,     /* FP32 iteration with FP64 reliable updates (Sec. 7.4 suggests
+                             mixed precision after Clark et al.); else FP64 throughout */
+  WZ_SOLVE_PC = 2         /* M0^-1 preconditioning of Sec. 7.3 (Eq. theprob); shift must be 0
+                             (a shifted system needs beta M0^-1dag M0^-1, Eq. yuier, not built) */
+};
+
+typedef struct wz_solve_stats {
+  int iterations;          /* max over right-hand sides of inner CG iterations */
+  int total_iterations;    /* sum over right-hand sides */
+  int reliable_updates;    /* sum over RHS of FP64 residual recomputations */
+  int converged;           /* right-hand sides that reached tol */
+  double max_true_residual;/* max over RHS of ||b - (M^dag M + shift) x|| / ||b||, FP64,
+                              of the ORIGINAL (unpreconditioned) system */
+  double seconds;          /* host wall time of the call, including the final sync */
+} wz_solve_stats;
+
+/* Solve (M^dagger M + shift) x = b for nrhs independent complex128 fields by
+ * conjugate gradient (Sec. 7.2, Eqs. theprob, yuier), x0 = 0.  Each RHS stops
+ * when its FP64 true relative residual ||b - A x|| / ||b|| <= tol (for
+ * WZ_SOLVE_PC: the residual of the preconditioned system; the original one
+ * is reported in stats).  b and x may be host or device pointers and must not
+ * alias.  Synchronous: returns after the solution is in x.  Returns
+ * WZ_NOT_CONVERGED (x = last iterate, stats filled) if maxiter inner
+ * iterations did not suffice for some RHS.  resid (may be NULL) receives
+ * nrhs FP64 true relative residuals of the original system. */
+int wz_solve(wz_ctx* ctx, const void* b, void* x, int nrhs, double shift, double tol, int maxiter,
+             unsigned flags, wz_solve_stats* stats, double* resid);
+
 #ifdef __cplusplus
 }
 #endif

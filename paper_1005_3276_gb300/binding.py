@@ -30,6 +30,18 @@ class WzParams(ctypes.Structure):
                 ("M0", ctypes.c_double), ("yukawa", ctypes.c_double)]
 
 
+class WzSolveStats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("total_iterations", ctypes.c_int),
+                ("reliable_updates", ctypes.c_int), ("converged", ctypes.c_int),
+                ("max_true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+WZ_SOLVE_MIXED, WZ_SOLVE_PC = 1, 2
+
+
 class WzError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"wz status {code}: {msg}")
@@ -48,6 +60,8 @@ def _load():
         "wz_supported_extent": ([I], I),
         "wz_set_phi": ([P, P], I),
         "wz_apply": ([P, I, I, P, P, I, D], I),
+        "wz_solve": ([P, P, P, I, D, D, I, ctypes.c_uint, ctypes.POINTER(WzSolveStats),
+                      ctypes.POINTER(ctypes.c_double)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -58,7 +72,8 @@ def _load():
 
 LIB = _load()
 
-EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply")
+EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply",
+           "wz_solve")
 
 
 def _is_torch(x):
@@ -134,6 +149,20 @@ def wz_apply(ctx, op, inp, out, nrhs, shift=0.0):
     return check(ctx, LIB.wz_apply(ctx, int(op), dt, pin, pout, int(nrhs), float(shift)))
 
 
+def wz_solve(ctx, b, x, nrhs, shift=0.0, tol=1e-10, maxiter=100000, flags=WZ_SOLVE_MIXED, resid=False,
+             raise_on_nonconvergence=True):
+    """Returns (status, stats dict, per-RHS true residuals or None)."""
+    pb, dt = field_ptr(b, WZ_C128)
+    px, _ = field_ptr(x, WZ_C128)
+    st = WzSolveStats()
+    res = (ctypes.c_double * max(int(nrhs), 1))() if resid else None
+    rc = LIB.wz_solve(ctx, pb, px, int(nrhs), float(shift), float(tol), int(maxiter), int(flags),
+                      ctypes.byref(st), res)
+    if rc not in (WZ_OK, WZ_NOT_CONVERGED) or (rc == WZ_NOT_CONVERGED and raise_on_nonconvergence):
+        check(ctx, rc)
+    return rc, st.as_dict(), (list(res)[:nrhs] if resid else None)
+
+
 class Lattice:
     """Owns one wz_ctx; methods forward to the C entry points of the same name."""
 
@@ -162,6 +191,16 @@ class Lattice:
 
     def set_phi(self, phi):
         return wz_set_phi(self.ctx, phi)
+
+    def _nrhs(self, f):
+        n = f.numel() if _is_torch(f) else f.size
+        return n // (4 * int(np.prod(self.dims)))
+
+    def solve(self, b, x, shift=0.0, tol=1e-10, maxiter=100000, mixed=True, pc=False, resid=False,
+              raise_on_nonconvergence=True):
+        flags = (WZ_SOLVE_MIXED if mixed else 0) | (WZ_SOLVE_PC if pc else 0)
+        return wz_solve(self.ctx, b, x, self._nrhs(b), shift, tol, maxiter, flags, resid,
+                        raise_on_nonconvergence)
 
     def apply(self, op, inp, out, nrhs=None, shift=0.0):
         if nrhs is None:

@@ -1,9 +1,13 @@
 // C ABI entry points: context, tables, phi, apply.
+#include <chrono>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "apply_impl.cuh"
+#include "solver.h"
+#include "wz_cg.cuh"
 #include "wz_ctx.h"
 
 namespace wz {
@@ -193,6 +197,45 @@ static int apply_typed(wz_ctx* c, int op, const void* in, void* out, int nrhs, d
   return WZ_OK;
 }
 
+
+// Per-RHS |b - Ax|^2 and |b|^2 (FP64), one block per right-hand side.
+__global__ void residual_norms_kernel(const cplx<double>* b, const cplx<double>* Ax, long n_per_rhs, double* out) {
+  __shared__ double red[33];
+  const long off = (long)blockIdx.x * n_per_rhs;
+  double rr = 0.0, bb = 0.0;
+  for (long i = threadIdx.x; i < n_per_rhs; i += blockDim.x) {
+    const cplx<double> bv = b[off + i], av = Ax[off + i];
+    const double dx = bv.x - av.x, dy = bv.y - av.y;
+    rr += dx * dx + dy * dy;
+    bb += bv.x * bv.x + bv.y * bv.y;
+  }
+  rr = block_sum(rr, red);
+  __syncthreads();
+  bb = block_sum(bb, red);
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = rr;
+    out[2 * blockIdx.x + 1] = bb;
+  }
+}
+
+// FP64 true relative residuals of (M^dag M + shift) x = b (device fields).
+static int true_residuals(wz_ctx* c, const cplx<double>* b, const cplx<double>* x, int nrhs, double shift,
+                          double* rel_out) {
+  const size_t field = sizeof(cplx<double>) * 4 * (size_t)c->V * nrhs;
+  WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAGM, nrhs) + field));
+  cplx<double>* Ax = (cplx<double>*)((char*)c->ws_apply.ptr + apply_ws_bytes<double>(c, WZ_OP_MDAGM, nrhs));
+  int rc = apply_op<double>(c, WZ_OP_MDAGM, x, Ax, nrhs, shift, (cplx<double>*)c->ws_apply.ptr);
+  if (rc) return rc;
+  WZ_CUDA_TRY(c, c->ws_red.reserve(sizeof(double) * 2 * nrhs));
+  residual_norms_kernel<<<nrhs, 256, 0, c->stream>>>(b, Ax, 4L * c->V, (double*)c->ws_red.ptr);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  double* h = (double*)c->host_pinned;
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(h, c->ws_red.ptr, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream));
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int j = 0; j < nrhs; ++j) rel_out[j] = h[2 * j + 1] > 0 ? sqrt(h[2 * j] / h[2 * j + 1]) : 0.0;
+  return WZ_OK;
+}
+
 }  // namespace wz
 
 using namespace wz;
@@ -276,6 +319,62 @@ int wz_apply(wz_ctx* c, int op, int dtype, const void* in, void* out, int nrhs, 
   if (dtype == WZ_C128) return apply_typed<double>(c, op, in, out, nrhs, shift);
   if (dtype == WZ_C64) return apply_typed<float>(c, op, in, out, nrhs, shift);
   return set_error(c, WZ_EINVAL, "wz_apply: unknown dtype");
+}
+
+int wz_solve(wz_ctx* c, const void* b, void* x, int nrhs, double shift, double tol, int maxiter, unsigned flags,
+             wz_solve_stats* stats, double* resid) {
+  if (!c) return WZ_EINVAL;
+  if (!b || !x || nrhs < 0 || tol <= 0.0 || maxiter < 1 || shift < 0.0)
+    return set_error(c, WZ_EINVAL, "wz_solve: bad argument");
+  if (b == x) return set_error(c, WZ_EINVAL, "wz_solve: b and x must not alias");
+  if ((flags & WZ_SOLVE_PC) && shift != 0.0)
+    return set_error(c, WZ_EINVAL, "wz_solve: M0^-1 preconditioning is defined for shift = 0 only");
+  const auto t0 = std::chrono::steady_clock::now();
+  if (nrhs == 0) {
+    if (stats) *stats = wz_solve_stats{};
+    return WZ_OK;
+  }
+  const size_t field = sizeof(cplx<double>) * 4 * (size_t)c->V * nrhs;
+  const bool db = is_device_pointer(b), dx = is_device_pointer(x);
+  const cplx<double>* pb = (const cplx<double>*)b;
+  cplx<double>* px = (cplx<double>*)x;
+  if (!db || !dx) {
+    WZ_CUDA_TRY(c, c->ws_stage.reserve(2 * field));
+    cplx<double>* sb = (cplx<double>*)c->ws_stage.ptr;
+    if (!db) {
+      WZ_CUDA_TRY(c, cudaMemcpyAsync(sb, b, field, cudaMemcpyHostToDevice, c->stream));
+      pb = sb;
+    }
+    if (!dx) px = sb + 4L * c->V * nrhs;
+  }
+  const bool pc = (flags & WZ_SOLVE_PC) != 0;
+  SolveOut o;
+  int rc = (flags & WZ_SOLVE_MIXED) ? solve_impl<float>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.1, &o)
+                                    : solve_impl<double>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.0, &o);
+  if (rc != WZ_OK && rc != WZ_NOT_CONVERGED) return rc;
+  if (pc || resid) {
+    std::vector<double> rel(nrhs);
+    int rc2 = true_residuals(c, pb, px, nrhs, shift, rel.data());
+    if (rc2) return rc2;
+    double mx = 0.0;
+    for (int j = 0; j < nrhs; ++j) mx = rel[j] > mx ? rel[j] : mx;
+    if (pc) o.max_true_residual = mx;
+    if (resid) memcpy(resid, rel.data(), sizeof(double) * nrhs);
+  }
+  if (!dx) {
+    WZ_CUDA_TRY(c, cudaMemcpyAsync(x, px, field, cudaMemcpyDeviceToHost, c->stream));
+  }
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (stats) {
+    stats->iterations = o.iterations;
+    stats->total_iterations = o.total_iterations;
+    stats->reliable_updates = o.reliable_updates;
+    stats->converged = o.converged;
+    stats->max_true_residual = o.max_true_residual;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (rc == WZ_NOT_CONVERGED) set_error(c, rc, "wz_solve: maxiter reached before tol");
+  return rc;
 }
 
 }  // extern "C"

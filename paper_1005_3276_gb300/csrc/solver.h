@@ -1,0 +1,22 @@
+// Solver entry shared between the C ABI and the solver translation units.
+#pragma once
+#include "wz_ctx.h"
+
+namespace wz {
+
+struct SolveOut {
+  int iterations = 0, total_iterations = 0, reliable_updates = 0, converged = 0;
+  double max_true_residual = 0.0;
+};
+
+// b, x: FP64 device fields.  RI = float: FP32 iteration with FP64 reliable
+// updates every time |r| drops by delta; RI = double: FP64 iteration.
+template <typename RI>
+int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, double shift, double tol, int maxiter,
+               bool pc, double delta, SolveOut* out);
+extern template int solve_impl<float>(wz_ctx*, const cplx<double>*, cplx<double>*, int, double, double, int, bool,
+                                      double, SolveOut*);
+extern template int solve_impl<double>(wz_ctx*, const cplx<double>*, cplx<double>*, int, double, double, int, bool,
+                                       double, SolveOut*);
+
+}  // namespace wz

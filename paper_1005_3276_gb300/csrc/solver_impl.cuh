@@ -1,0 +1,259 @@
+// Host sequencing of the fused CG solver (see wz_cg.cuh for the algorithm).
+//
+// The iteration passes are issued in chunks of K iterations followed by one
+// reliable-update block; every kernel gates itself per right-hand side on the
+// device state, so a chunk is a fixed launch sequence and the host only reads
+// the per-RHS state between chunks to see whether all have finished.
+#pragma once
+#include <chrono>
+#include <cstring>
+#include <vector>
+
+#include "apply_impl.cuh"
+#include "solver.h"
+#include "wz_cg.cuh"
+
+namespace wz {
+
+template <typename R, typename LO, int L, int MODE, bool PC>
+static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
+  using S = XYShape<L>;
+  const size_t smem = sizeof(cplx<R>) * S::PLANE * S::PPC + 33 * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = set_smem(xy_cg<R, LO, L, MODE, PC>, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  dim3 grid(a.nblk, nrhs);
+  xy_cg<R, LO, L, MODE, PC><<<grid, S::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename R, typename LO, int L, bool PC>
+static cudaError_t launch_cg_m(int mode, const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
+  switch (mode) {
+    case CG_P1: return launch_cg_t<R, LO, L, CG_P1, PC>(a, nrhs, st);
+    case CG_P3: return launch_cg_t<R, LO, L, CG_P3, PC>(a, nrhs, st);
+    case CG_P5: return launch_cg_t<R, LO, L, CG_P5, PC>(a, nrhs, st);
+    case RU_P1: return launch_cg_t<R, LO, L, RU_P1, PC>(a, nrhs, st);
+    case RU_P5: return launch_cg_t<R, LO, L, RU_P5, PC>(a, nrhs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, typename LO>
+static cudaError_t launch_cg(int L, bool pc, int mode, const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
+  switch (L) {
+#define WZ_CASE(n)                                                           \
+  case n:                                                                    \
+    return pc ? launch_cg_m<R, LO, n, true>(mode, a, nrhs, st)               \
+              : launch_cg_m<R, LO, n, false>(mode, a, nrhs, st);
+    WZ_FOR_EXTENTS(WZ_CASE)
+#undef WZ_CASE
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <int L> static int nblk_of(int TZ) { return (TZ + XYShape<L>::PPC - 1) / XYShape<L>::PPC; }
+static int xy_nblk(int L, int TZ) {
+  switch (L) {
+#define WZ_CASE(n) \
+  case n: return nblk_of<n>(TZ);
+    WZ_FOR_EXTENTS(WZ_CASE)
+#undef WZ_CASE
+  }
+  return 0;
+}
+
+// Workspace layout (bytes) for a solve with iteration type RI.
+template <typename RI> struct SolverWS {
+  size_t field_ri, field64, off_xlo, off_r, off_p, off_A, off_C, off_A64, off_C64, off_bt, off_xt, off_part,
+      off_st, total;
+  SolverWS(long V, int nrhs, int nblk, bool pc) {
+    field_ri = sizeof(cplx<RI>) * 4 * (size_t)V * nrhs;
+    field64 = sizeof(cplx<double>) * 4 * (size_t)V * nrhs;
+    size_t o = 0;
+    auto take = [&](size_t n) {
+      size_t r = o;
+      o += (n + 255) & ~size_t(255);
+      return r;
+    };
+    off_xlo = take(field_ri);
+    off_r = take(field_ri);
+    off_p = take(field_ri);
+    off_A = take(field_ri);
+    off_C = take(field_ri);
+    off_A64 = take(field64);
+    off_C64 = take(field64);
+    off_bt = pc ? take(field64) : 0;
+    off_xt = pc ? take(field64) : 0;
+    off_part = take(sizeof(double) * 3 * (size_t)nrhs * (nblk > 64 ? nblk : 64));
+    off_st = take(sizeof(RhsState) * nrhs);
+    total = o;
+  }
+};
+
+// b, x: FP64 device fields.  RI: iteration precision (float: mixed, double: FP64).
+template <typename RI>
+int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, double shift, double tol, int maxiter,
+               bool pc, double delta, SolveOut* out) {
+  const int L = c->X;
+  const int TZ = c->T * c->Z;
+  const int nblk = xy_nblk(L, TZ);
+  SolverWS<RI> W(c->V, nrhs, nblk, pc);
+  WZ_CUDA_TRY(c, c->ws_solver.reserve(W.total));
+  char* base = (char*)c->ws_solver.ptr;
+  cplx<RI>* xlo = (cplx<RI>*)(base + W.off_xlo);
+  cplx<RI>* r = (cplx<RI>*)(base + W.off_r);
+  cplx<RI>* p = (cplx<RI>*)(base + W.off_p);
+  cplx<RI>* A = (cplx<RI>*)(base + W.off_A);
+  cplx<RI>* Cb = (cplx<RI>*)(base + W.off_C);
+  cplx<double>* A64 = (cplx<double>*)(base + W.off_A64);
+  cplx<double>* C64 = (cplx<double>*)(base + W.off_C64);
+  const int npart = nblk > 64 ? nblk : 64;
+  double* part3 = (double*)(base + W.off_part);
+  double* part5 = part3 + (size_t)nrhs * npart;
+  double* partR = part5 + (size_t)nrhs * npart;
+  RhsState* st = (RhsState*)(base + W.off_st);
+  cudaStream_t s = c->stream;
+  const long n_per_rhs = 4L * c->V;
+
+  // preconditioned problem: b~ = (M0^-1)^dag b, solve for x~ = M0 x
+  const cplx<double>* bs = b;
+  cplx<double>* xs = x;
+  if (pc) {
+    cplx<double>* bt = (cplx<double>*)(base + W.off_bt);
+    cplx<double>* xt = (cplx<double>*)(base + W.off_xt);
+    int rc = apply_op<double>(c, WZ_OP_M0INV_DAG, b, bt, nrhs, 0.0, A64);
+    if (rc) return rc;
+    bs = bt;
+    xs = xt;
+  }
+
+  WZ_CUDA_TRY(c, cudaMemsetAsync(xs, 0, W.field64, s));
+  cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, n_per_rhs, partR, 64);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+
+  const int gate_stride = sizeof(RhsState) / sizeof(int);
+  const int* gate_run = &st->run;
+  const int* gate_ru = &st->ru;
+
+  CGArgs<RI, RI> ga{};
+  ga.A = A;
+  ga.Cb = Cb;
+  ga.p = p;
+  ga.r = r;
+  ga.x = xlo;
+  ga.phi = phi_of<RI>(c);
+  ga.k = site_coef_of<RI>(c);
+  ga.shift = shift;
+  ga.st = st;
+  ga.nblk = nblk;
+  ga.TZ = TZ;
+  ga.gate_ru = 0;
+
+  CGArgs<double, RI> ra{};
+  ra.A = A64;
+  ra.Cb = C64;
+  ra.p = xs;  // x_hi
+  ra.lo_x = xlo;
+  ra.lo_r = r;
+  ra.b = bs;
+  ra.phi = c->phi64;
+  ra.k = site_coef_of<double>(c);
+  ra.shift = shift;
+  ra.st = st;
+  ra.nblk = nblk;
+  ra.TZ = TZ;
+  ra.gate_ru = 1;
+
+  ZTArgs<RI> z1 = zt_args<RI>(c, RI(1)), z2 = zt_args<RI>(c, RI(-1));
+  z1.A = z2.A = A;
+  z1.gate = z2.gate = gate_run;
+  z1.gate_stride = z2.gate_stride = gate_stride;
+  ZTArgs<double> y1 = zt_args<double>(c, 1.0), y2 = zt_args<double>(c, -1.0);
+  y1.A = y2.A = A64;
+  y1.gate = y2.gate = gate_ru;
+  y1.gate_stride = y2.gate_stride = gate_stride;
+  const int mul1 = pc ? ZT_M0INV : ZT_DSLASH, mul2 = pc ? ZT_M0INV_DAG : ZT_DSLASH;
+
+  const double tol2 = tol * tol, delta2 = delta * delta;
+  const int K = 8;
+  RhsState* hst = (RhsState*)c->host_pinned;
+  if (sizeof(RhsState) * nrhs > (1 << 16)) return set_error(c, WZ_EINVAL, "too many right-hand sides");
+  cudaError_t e;
+#define WZ_RUN(...)                                                 \
+  do {                                                              \
+    e = (__VA_ARGS__);                                              \
+    if (e != cudaSuccess) return cuda_error(c, e, #__VA_ARGS__);    \
+  } while (0)
+  const int max_chunks = maxiter / K + 64;
+  for (int chunk = 0; chunk < max_chunks; ++chunk) {
+    for (int k = 0; k < K; ++k) {
+      CGArgs<RI, RI> a1 = ga;
+      WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P1, a1, nrhs, s));
+      WZ_RUN(launch_zt<RI>(c->Z, c->T, mul1, z1, nrhs, s));
+      CGArgs<RI, RI> a3 = ga;
+      a3.part_out = part3;
+      WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P3, a3, nrhs, s));
+      WZ_RUN(launch_zt<RI>(c->Z, c->T, mul2, z2, nrhs, s));
+      CGArgs<RI, RI> a5 = ga;
+      a5.part_in = part3;
+      a5.part_out = part5;
+      WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, s));
+      cg_scalar_iter<<<nrhs, 32, 0, s>>>(st, part5, nblk, tol2, delta2, maxiter);
+      WZ_RUN(cudaGetLastError());
+    }
+    // reliable update / true residual for the RHS that asked for one
+    WZ_RUN(launch_cg<double, RI>(L, pc, RU_P1, ra, nrhs, s));
+    WZ_RUN(launch_zt<double>(c->Z, c->T, mul1, y1, nrhs, s));
+    {
+      CGArgs<double, double> r3{};
+      r3.A = A64;
+      r3.Cb = C64;
+      r3.p = xs;
+      r3.phi = c->phi64;
+      r3.k = ra.k;
+      r3.shift = shift;
+      r3.st = st;
+      r3.nblk = nblk;
+      r3.TZ = TZ;
+      r3.gate_ru = 1;
+      WZ_RUN(launch_cg<double, double>(L, pc, CG_P3, r3, nrhs, s));
+    }
+    WZ_RUN(launch_zt<double>(c->Z, c->T, mul2, y2, nrhs, s));
+    CGArgs<double, RI> r5 = ra;
+    r5.part_out = partR;
+    WZ_RUN(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, s));
+    cg_scalar_ru<<<nrhs, 32, 0, s>>>(st, partR, nblk, tol2, maxiter);
+    WZ_RUN(cudaGetLastError());
+    WZ_RUN(cudaMemcpyAsync(hst, st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, s));
+    WZ_RUN(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int j = 0; j < nrhs; ++j) any |= hst[j].active != 0;
+    if (!any) break;
+  }
+#undef WZ_RUN
+
+  if (pc) {
+    int rc = apply_op<double>(c, WZ_OP_M0INV, xs, x, nrhs, 0.0, A64);
+    if (rc) return rc;
+  }
+  SolveOut o;
+  for (int j = 0; j < nrhs; ++j) {
+    o.iterations = hst[j].iters > o.iterations ? hst[j].iters : o.iterations;
+    o.total_iterations += hst[j].iters;
+    o.reliable_updates += hst[j].ru_count;
+    const bool ok = hst[j].active == 0 && hst[j].status == WZ_OK;
+    o.converged += ok ? 1 : 0;
+    const double rel = hst[j].bnorm2 > 0 ? sqrt(hst[j].rtrue2 / hst[j].bnorm2) : 0.0;
+    o.max_true_residual = rel > o.max_true_residual ? rel : o.max_true_residual;
+  }
+  *out = o;
+  return o.converged == nrhs ? WZ_OK : WZ_NOT_CONVERGED;
+}
+
+}  // namespace wz

@@ -1,0 +1,281 @@
+// Conjugate gradient on M^dagger M + sigma fused into the plane passes.
+//
+// CG on the Hermitian positive-definite operator A = M^dagger M + sigma
+// (Eq. theprob, Eq. yuier; sigma = 0 for the plain problem), one independent
+// recursion per right-hand side, all right-hand sides in the same launches.
+// One iteration is five plane passes plus a one-warp-per-RHS scalar kernel:
+//
+//   P1 (xy)  p = r + beta p ; A = F_xy p
+//   P2 (zt)  A <- Dslash(p) A                  (M0^-1(p) when preconditioned)
+//   P3 (xy)  C = M p (position space) ; A = F_xy C' ; partial |C|^2 + sigma |p|^2
+//   P4 (zt)  A <- -Dslash(p) A                 ((M0^-1)^dag(p) when preconditioned)
+//   P5 (xy)  Ap = M^dag C + sigma p ; alpha = rr / (p.Ap) ; x += alpha p ;
+//            r -= alpha Ap ; partial |r|^2
+//   S        rr_new, beta = rr_new / rr, reliable-update and stop tests
+//
+// p.Ap = |M p|^2 + sigma |p|^2 is known after P3, so P5 does the vector
+// updates without storing Ap.  Reductions are deterministic: per-thread
+// partials, a fixed warp/block tree, one partial per block, and every
+// consumer sums the block partials in the same order.
+//
+// Mixed precision (reliable updates, Clark et al. 2010; Sleijpen and van der
+// Vorst 1996): the recursion runs in FP32; when |r| has dropped below delta
+// times its value at the last update (or below tol |b|), the FP32 iterate is
+// folded into the FP64 solution and the residual is recomputed in FP64:
+//
+//   RU_P1 (xy, FP64) x_hi += x_lo ; x_lo = 0 ; A = F_xy x_hi
+//   zt, P3, zt       (FP64 M^dagger M as above)
+//   RU_P5 (xy, FP64) r = b - (M^dag M + sigma) x_hi ; r_lo = (float) r ; partial |r|^2
+//   S_ru             converged if |r| <= tol |b|, else beta = |r|^2 / rr_prev
+//
+// The pure FP64 solver is the same code with FP64 iteration vectors and
+// delta = 0 (the update then only runs as the final true-residual check).
+#pragma once
+#include "wz_kernels.cuh"
+
+namespace wz {
+
+struct RhsState {
+  double rr;       // |r|^2 of the recursive residual
+  double rr_prev;  // previous |r|^2 (beta after a reliable update)
+  double beta;     // beta of the next direction update
+  double bnorm2;   // |b|^2
+  double rmax2;    // |r|^2 at the last reliable update
+  double rtrue2;   // |b - A x|^2 at the last reliable update (FP64)
+  int run;         // iteration passes act on this RHS
+  int ru;          // reliable update pending
+  int active;      // not finished
+  int iters;       // inner iterations
+  int ru_count;    // reliable updates done (FP64 applies)
+  int status;      // WZ_OK or WZ_NOT_CONVERGED
+};
+
+enum CGMode { CG_P1 = 0, CG_P3, CG_P5, RU_P1, RU_P5 };
+
+template <typename R, typename LO> struct CGArgs {
+  cplx<R>* A;           // momentum intermediate (in place)
+  cplx<R>* Cb;          // M p (or M~ p) in position space
+  cplx<R>* p;           // search direction; x_hi for the RU passes
+  cplx<R>* r;           // residual (iteration precision)
+  cplx<R>* x;           // iterate accumulated between reliable updates
+  cplx<LO>* lo_x;       // RU_P1: low-precision iterate folded in and zeroed
+  cplx<LO>* lo_r;       // RU_P5: residual written in the iteration precision
+  const cplx<R>* b;     // RU_P5: right-hand side
+  const cplx<R>* phi;
+  SiteCoef<R> k;
+  double shift;
+  RhsState* st;
+  double* part_out;     // [rhs][nblk] block partials written by this pass (may be null)
+  const double* part_in;  // [rhs][nblk] block partials of p.Ap (CG_P5)
+  int nblk;             // blocks per right-hand side
+  int TZ;               // planes per right-hand side
+  int gate_ru;          // 1: act on RHS with a pending reliable update; 0: on running RHS
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum of v over the block, valid on thread 0.  Whole warps only.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  return t;
+}
+
+// Sum of the nblk partials of one RHS, in a fixed order; valid on lane 0.
+__device__ __forceinline__ double sum_partials(const double* part, int nblk) {
+  const int lane = threadIdx.x & 31;
+  double t = 0.0;
+  for (int i = lane; i < nblk; i += 32) t += part[i];
+  return warp_sum(t);
+}
+
+template <typename R> __device__ __forceinline__ R norm2(cplx<R> a) { return a.x * a.x + a.y * a.y; }
+
+template <typename R, typename LO, int L, int MODE, bool PC>
+__global__ void __launch_bounds__(XYShape<L>::THREADS)
+xy_cg(CGArgs<R, LO> a) {
+  using S = XYShape<L>;
+  using H = XYPhase<R, L>;
+  constexpr bool INV = (MODE == CG_P3 || MODE == CG_P5 || MODE == RU_P5);
+  constexpr bool FWD = (MODE == CG_P1 || MODE == CG_P3 || MODE == RU_P1);
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
+  double* red = reinterpret_cast<double*>(sm + S::PLANE * S::PPC);  // 33 doubles
+
+  const int rhs = blockIdx.y;
+  RhsState* st = a.st + rhs;
+  if (!(a.gate_ru ? st->ru : st->run)) return;  // whole block, before any barrier
+
+  const int tid = threadIdx.x;
+  const int pl_local = tid / S::TPP;
+  const int w = (tid / 4) % L;
+  const int s = tid & 3;
+  const int plane_in = blockIdx.x * S::PPC + pl_local;
+  const bool live = plane_in < a.TZ;
+  const long plane = (long)rhs * a.TZ + plane_in;
+  cplx<R>* P = sm + pl_local * S::PLANE;
+  const long base = plane * (long)(L * L) * 4;
+
+  cplx<R> v[L];
+  R part = R(0);
+
+  if constexpr (MODE == CG_P5) {
+    // alpha = rr / p.Ap from the P3 partials: the same sum in every block
+    if (tid < 32) {
+      const double pAp = sum_partials(a.part_in + (long)rhs * a.nblk, a.nblk);
+      if (tid == 0) red[32] = pAp > 0.0 ? st->rr / pAp : 0.0;
+    }
+  }
+  if (INV) {
+    if (live) H::inv_x(a.A + base, P, w, s, v);
+    __syncthreads();
+  }
+  R alpha = R(0), beta = R(0);
+  if constexpr (MODE == CG_P5) alpha = (R)red[32];
+  if constexpr (MODE == CG_P1) beta = (R)st->beta;
+  const R sigma = (R)a.shift;
+
+  if (live) {
+    const int x = w;
+    const long site0 = plane * (long)(L * L) + x;
+    const long phib = (long)plane_in * (L * L) + x;
+    if (INV) H::inv_y(P, w, s, v);
+#pragma unroll
+    for (int y = 0; y < L; ++y) {
+      const long e = (site0 + y * L) * 4 + s;
+      if constexpr (MODE == CG_P1) {
+        const cplx<R> pv = a.r[e] + beta * a.p[e];
+        a.p[e] = pv;
+        v[y] = pv;
+      } else if constexpr (MODE == CG_P3) {
+        const cplx<R> pe = a.p[e];
+        const cplx<R> f = a.phi[phib + y * L];
+        if constexpr (PC) v[y] = pe + site_coef<R, false, false>(a.k, f, s) * v[y];
+        else v[y] = v[y] + site_coef<R, false, true>(a.k, f, s) * pe;
+        a.Cb[e] = v[y];
+        part += norm2(v[y]) + sigma * norm2(pe);
+        if constexpr (PC) v[y] = site_coef<R, true, false>(a.k, f, s) * v[y];
+      } else if constexpr (MODE == CG_P5 || MODE == RU_P5) {
+        const cplx<R> pe = a.p[e];  // p, or x_hi for RU_P5
+        cplx<R> ap;
+        if constexpr (PC) ap = a.Cb[e] + v[y];
+        else ap = v[y] + site_coef<R, true, true>(a.k, a.phi[phib + y * L], s) * a.Cb[e];
+        ap = ap + sigma * pe;
+        if constexpr (MODE == CG_P5) {
+          a.x[e] = a.x[e] + alpha * pe;
+          const cplx<R> rn = a.r[e] - alpha * ap;
+          a.r[e] = rn;
+          part += norm2(rn);
+        } else {
+          const cplx<R> rn = a.b[e] - ap;
+          a.lo_r[e] = cplx<LO>{(LO)rn.x, (LO)rn.y};
+          part += norm2(rn);
+        }
+      } else if constexpr (MODE == RU_P1) {
+        const cplx<LO> xl = a.lo_x[e];
+        const cplx<R> xv = a.p[e] + cplx<R>{(R)xl.x, (R)xl.y};
+        a.p[e] = xv;
+        a.lo_x[e] = cplx<LO>{LO(0), LO(0)};
+        v[y] = xv;
+      }
+    }
+    if (FWD) H::fwd_y(v, P, w, s);
+  }
+  if constexpr (FWD) {
+    __syncthreads();
+    if (live) H::fwd_x(P, a.A + base, w, s, v);
+  }
+  if (a.part_out) {
+    const double t = block_sum((double)part, red);
+    if (tid == 0) a.part_out[(long)rhs * a.nblk + blockIdx.x] = t;
+  }
+}
+
+// r = (R) b, x = 0, partial |b|^2 (FP64).  Grid (nblk, nrhs), one thread per complex.
+template <typename R>
+__global__ void cg_init(const cplx<double>* b, cplx<R>* r, cplx<R>* x, long n_per_rhs, double* part, int nblk) {
+  __shared__ double red[33];
+  const int rhs = blockIdx.y;
+  double t = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n_per_rhs; i += (long)nblk * blockDim.x) {
+    const long e = (long)rhs * n_per_rhs + i;
+    const cplx<double> bv = b[e];
+    r[e] = cplx<R>{(R)bv.x, (R)bv.y};
+    x[e] = cplx<R>{R(0), R(0)};
+    t += bv.x * bv.x + bv.y * bv.y;
+  }
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) part[(long)rhs * nblk + blockIdx.x] = t;
+}
+
+// One warp per RHS.
+static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk) {
+  RhsState* s = st + blockIdx.x;
+  const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
+  if (threadIdx.x == 0) {
+    s->bnorm2 = t;
+    s->rr = t;
+    s->rr_prev = t;
+    s->beta = 0.0;
+    s->rmax2 = t;
+    s->rtrue2 = t;
+    s->iters = 0;
+    s->ru_count = 0;
+    s->ru = 0;
+    s->status = WZ_OK;
+    s->active = t > 0.0;
+    s->run = t > 0.0;
+  }
+}
+
+static __global__ void cg_scalar_iter(RhsState* st, const double* part, int nblk, double tol2, double delta2, int maxiter) {
+  RhsState* s = st + blockIdx.x;
+  if (!s->run) return;
+  const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
+  if (threadIdx.x == 0) {
+    s->iters += 1;
+    s->beta = t / s->rr;
+    s->rr_prev = s->rr;
+    s->rr = t;
+    if (t <= delta2 * s->rmax2 || t <= tol2 * s->bnorm2 || s->iters >= maxiter) {
+      s->ru = 1;
+      s->run = 0;
+    }
+  }
+}
+
+static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, double tol2, int maxiter) {
+  RhsState* s = st + blockIdx.x;
+  if (!s->ru) return;
+  const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
+  if (threadIdx.x == 0) {
+    s->ru = 0;
+    s->ru_count += 1;
+    s->rtrue2 = t;
+    if (t <= tol2 * s->bnorm2) {
+      s->active = 0;
+      s->run = 0;
+      s->status = WZ_OK;
+    } else if (s->iters >= maxiter) {
+      s->active = 0;
+      s->run = 0;
+      s->status = WZ_NOT_CONVERGED;
+    } else {
+      s->beta = t / s->rr_prev;
+      s->rr = t;
+      s->rmax2 = t;
+      s->run = 1;
+    }
+  }
+}
+
+}  // namespace wz

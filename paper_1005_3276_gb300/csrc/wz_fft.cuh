@@ -31,8 +31,8 @@ template <typename R> WZ_HD cplx<R> mul_mi(cplx<R> a) { return {a.y, -a.x}; }
 // a * conj(b) summed real part helpers
 template <typename R> WZ_HD R re_conj_mul(cplx<R> a, cplx<R> b) { return a.x * b.x + a.y * b.y; }
 
-__constant__ double c_tw64[WZ_TW_N] = {WZ_TW_TABLE};
-__constant__ float c_tw32[WZ_TW_N] = {WZ_TW_TABLE};
+static __constant__ double c_tw64[WZ_TW_N] = {WZ_TW_TABLE};
+static __constant__ float c_tw32[WZ_TW_N] = {WZ_TW_TABLE};
 // host copies so that the same templates can be exercised on the CPU
 static const double h_tw64[WZ_TW_N] = {WZ_TW_TABLE};
 

@@ -78,13 +78,57 @@ template <typename R> struct XYArgs {
   int TZ;                // planes per right-hand side
 };
 
-// Threads per plane: 4 * L (one per (line, spin)); PPC planes per block.
+// Threads per plane: 4 * L (one per (line, spin)); PPC planes per block, the
+// largest count with at most 256 threads and whole warps (block reductions
+// shuffle over full warps).
+constexpr int xy_ppc(int tpp) {
+  int best = 1;
+  for (int k = 1; k * tpp <= 256; ++k)
+    if ((k * tpp) % 32 == 0) best = k;
+  return best;
+}
 template <int L> struct XYShape {
   static constexpr int TPP = 4 * L;
-  static constexpr int PPC = (256 / TPP) > 0 ? (256 / TPP) : 1;
+  static constexpr int PPC = xy_ppc(TPP);
   static constexpr int THREADS = TPP * PPC;
   static constexpr int RP = 4 * (L + 1);  // smem row pitch (complex), one site of padding
   static constexpr int PLANE = L * RP;
+  static_assert(THREADS % 32 == 0, "xy block must be whole warps");
+};
+
+// Phase helpers shared by the xy kernels.  A thread owns (line w, spin s) of
+// the plane P in shared memory (row pitch RP, one site of padding per row).
+template <typename R, int L> struct XYPhase {
+  using S = XYShape<L>;
+  // phase A: inverse FFT along x of momentum row y = w (global), result into P
+  static __device__ __forceinline__ void inv_x(const cplx<R>* Ap, cplx<R>* P, int w, int s, cplx<R> (&v)[L]) {
+#pragma unroll
+    for (int x = 0; x < L; ++x) v[x] = Ap[(w * L + x) * 4 + s];
+    fft_line<L, +1, R>(v);
+#pragma unroll
+    for (int x = 0; x < L; ++x) P[w * S::RP + x * 4 + s] = v[x];
+  }
+  // phase B entry: column x = w of P, inverse FFT along y -> position space
+  static __device__ __forceinline__ void inv_y(const cplx<R>* P, int w, int s, cplx<R> (&v)[L]) {
+#pragma unroll
+    for (int y = 0; y < L; ++y) v[y] = P[y * S::RP + w * 4 + s];
+    fft_line<L, +1, R>(v);
+  }
+  // phase B exit: forward FFT along y, column x = w back into P (the same
+  // cells inv_y of this thread read, so no barrier is needed before it)
+  static __device__ __forceinline__ void fwd_y(cplx<R> (&v)[L], cplx<R>* P, int w, int s) {
+    fft_line<L, -1, R>(v);
+#pragma unroll
+    for (int y = 0; y < L; ++y) P[y * S::RP + w * 4 + s] = v[y];
+  }
+  // phase C: row p_y = w of P, forward FFT along x, store momentum output
+  static __device__ __forceinline__ void fwd_x(const cplx<R>* P, cplx<R>* Ap, int w, int s, cplx<R> (&v)[L]) {
+#pragma unroll
+    for (int x = 0; x < L; ++x) v[x] = P[w * S::RP + x * 4 + s];
+    fft_line<L, -1, R>(v);
+#pragma unroll
+    for (int x = 0; x < L; ++x) Ap[(w * L + x) * 4 + s] = v[x];
+  }
 };
 
 template <typename R, int L, int MODE>
@@ -198,6 +242,8 @@ template <typename R> struct ZTArgs {
   R m_re, m_im;
   int ntiles;          // ceil(XY / C)
   int X, XY;
+  const int* gate;     // optional per-RHS run flag: block returns if gate[rhs * gate_stride] == 0
+  int gate_stride;
 };
 
 // Columns per block: 256 B contiguous per (z, t) row for short lines, fewer
@@ -227,6 +273,7 @@ zt_pass(ZTArgs<R> a) {
   const int c = (tid >> 2) % C;
   const int q = tid / (4 * C);  // t in the z-phase, z in the t-phase
   const int rhs = blockIdx.x / a.ntiles;
+  if (a.gate && !a.gate[(long)rhs * a.gate_stride]) return;  // whole block, before any barrier
   const int col_raw = (blockIdx.x % a.ntiles) * C + c;  // (y, x) column = y * X + x
   // the last tile may be ragged (X * Y not a multiple of C): lanes past the
   // end keep computing on zeros so that every warp stays whole for the

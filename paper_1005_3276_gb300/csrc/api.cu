@@ -198,44 +198,6 @@ static int apply_typed(wz_ctx* c, int op, const void* in, void* out, int nrhs, d
 }
 
 
-// Per-RHS |b - Ax|^2 and |b|^2 (FP64), one block per right-hand side.
-__global__ void residual_norms_kernel(const cplx<double>* b, const cplx<double>* Ax, long n_per_rhs, double* out) {
-  __shared__ double red[33];
-  const long off = (long)blockIdx.x * n_per_rhs;
-  double rr = 0.0, bb = 0.0;
-  for (long i = threadIdx.x; i < n_per_rhs; i += blockDim.x) {
-    const cplx<double> bv = b[off + i], av = Ax[off + i];
-    const double dx = bv.x - av.x, dy = bv.y - av.y;
-    rr += dx * dx + dy * dy;
-    bb += bv.x * bv.x + bv.y * bv.y;
-  }
-  rr = block_sum(rr, red);
-  __syncthreads();
-  bb = block_sum(bb, red);
-  if (threadIdx.x == 0) {
-    out[2 * blockIdx.x] = rr;
-    out[2 * blockIdx.x + 1] = bb;
-  }
-}
-
-// FP64 true relative residuals of (M^dag M + shift) x = b (device fields).
-static int true_residuals(wz_ctx* c, const cplx<double>* b, const cplx<double>* x, int nrhs, double shift,
-                          double* rel_out) {
-  const size_t field = sizeof(cplx<double>) * 4 * (size_t)c->V * nrhs;
-  WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAGM, nrhs) + field));
-  cplx<double>* Ax = (cplx<double>*)((char*)c->ws_apply.ptr + apply_ws_bytes<double>(c, WZ_OP_MDAGM, nrhs));
-  int rc = apply_op<double>(c, WZ_OP_MDAGM, x, Ax, nrhs, shift, (cplx<double>*)c->ws_apply.ptr);
-  if (rc) return rc;
-  WZ_CUDA_TRY(c, c->ws_red.reserve(sizeof(double) * 2 * nrhs));
-  residual_norms_kernel<<<nrhs, 256, 0, c->stream>>>(b, Ax, 4L * c->V, (double*)c->ws_red.ptr);
-  WZ_CUDA_TRY(c, cudaGetLastError());
-  double* h = (double*)c->host_pinned;
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(h, c->ws_red.ptr, sizeof(double) * 2 * nrhs, cudaMemcpyDeviceToHost, c->stream));
-  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  for (int j = 0; j < nrhs; ++j) rel_out[j] = h[2 * j + 1] > 0 ? sqrt(h[2 * j] / h[2 * j + 1]) : 0.0;
-  return WZ_OK;
-}
-
 }  // namespace wz
 
 using namespace wz;
@@ -267,7 +229,7 @@ int wz_create(const wz_params* p, void* stream, wz_ctx** out) {
     if (e == cudaSuccess) e = cudaMalloc(&c->phi32, sizeof(cplx<float>) * c->V);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->phi64, 0, sizeof(cplx<double>) * c->V, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->phi32, 0, sizeof(cplx<float>) * c->V, c->stream);
-    if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, 1 << 16);
+    if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, WZ_PINNED_BYTES);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) rc = cuda_error(c, e, "wz_create");
   }
@@ -352,14 +314,11 @@ int wz_solve(wz_ctx* c, const void* b, void* x, int nrhs, double shift, double t
   int rc = (flags & WZ_SOLVE_MIXED) ? solve_impl<float>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.1, &o)
                                     : solve_impl<double>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.0, &o);
   if (rc != WZ_OK && rc != WZ_NOT_CONVERGED) return rc;
-  if (pc || resid) {
+  if (resid) {
     std::vector<double> rel(nrhs);
     int rc2 = true_residuals(c, pb, px, nrhs, shift, rel.data());
     if (rc2) return rc2;
-    double mx = 0.0;
-    for (int j = 0; j < nrhs; ++j) mx = rel[j] > mx ? rel[j] : mx;
-    if (pc) o.max_true_residual = mx;
-    if (resid) memcpy(resid, rel.data(), sizeof(double) * nrhs);
+    memcpy(resid, rel.data(), sizeof(double) * nrhs);
   }
   if (!dx) {
     WZ_CUDA_TRY(c, cudaMemcpyAsync(x, px, field, cudaMemcpyDeviceToHost, c->stream));

@@ -19,4 +19,9 @@ extern template int solve_impl<float>(wz_ctx*, const cplx<double>*, cplx<double>
 extern template int solve_impl<double>(wz_ctx*, const cplx<double>*, cplx<double>*, int, double, double, int, bool,
                                        double, SolveOut*);
 
+// FP64 true relative residuals of (M^dag M + shift) x = b for nrhs device
+// fields; uses the apply workspace and synchronises the context stream.
+int true_residuals(wz_ctx* c, const cplx<double>* b, const cplx<double>* x, int nrhs, double shift,
+                   double* rel_out);
+
 }  // namespace wz

@@ -134,7 +134,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   WZ_CUDA_TRY(c, cudaMemsetAsync(xs, 0, W.field64, s));
   cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, n_per_rhs, partR, 64);
   WZ_CUDA_TRY(c, cudaGetLastError());
-  cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64);
+  cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol);
   WZ_CUDA_TRY(c, cudaGetLastError());
 
   const int gate_stride = sizeof(RhsState) / sizeof(int);
@@ -180,10 +180,10 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   y1.gate_stride = y2.gate_stride = gate_stride;
   const int mul1 = pc ? ZT_M0INV : ZT_DSLASH, mul2 = pc ? ZT_M0INV_DAG : ZT_DSLASH;
 
-  const double tol2 = tol * tol, delta2 = delta * delta;
+  const double delta2 = delta * delta;
   const int K = 8;
   RhsState* hst = (RhsState*)c->host_pinned;
-  if (sizeof(RhsState) * nrhs > (1 << 16)) return set_error(c, WZ_EINVAL, "too many right-hand sides");
+  if (sizeof(RhsState) * nrhs > WZ_PINNED_SCRATCH_OFFSET) return set_error(c, WZ_EINVAL, "too many right-hand sides");
   cudaError_t e;
 #define WZ_RUN(...)                                                 \
   do {                                                              \
@@ -191,6 +191,11 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     if (e != cudaSuccess) return cuda_error(c, e, #__VA_ARGS__);    \
   } while (0)
   const int max_chunks = maxiter / K + 64;
+  // The preconditioned recursion stops on the residual of M~^dag M~ x~ = b~;
+  // the original residual b - M^dag M x = M0^dag (b~ - M~^dag M~ x~) is then
+  // checked in FP64 and RHS that miss tol resume with a tighter tolerance.
+  std::vector<double> rel(nrhs);
+  for (int outer = 0; outer < 8; ++outer) {
   for (int chunk = 0; chunk < max_chunks; ++chunk) {
     for (int k = 0; k < K; ++k) {
       CGArgs<RI, RI> a1 = ga;
@@ -204,7 +209,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       a5.part_in = part3;
       a5.part_out = part5;
       WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, s));
-      cg_scalar_iter<<<nrhs, 32, 0, s>>>(st, part5, nblk, tol2, delta2, maxiter);
+      cg_scalar_iter<<<nrhs, 32, 0, s>>>(st, part5, nblk, delta2, maxiter);
       WZ_RUN(cudaGetLastError());
     }
     // reliable update / true residual for the RHS that asked for one
@@ -228,7 +233,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     CGArgs<double, RI> r5 = ra;
     r5.part_out = partR;
     WZ_RUN(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, s));
-    cg_scalar_ru<<<nrhs, 32, 0, s>>>(st, partR, nblk, tol2, maxiter);
+    cg_scalar_ru<<<nrhs, 32, 0, s>>>(st, partR, nblk, maxiter);
     WZ_RUN(cudaGetLastError());
     WZ_RUN(cudaMemcpyAsync(hst, st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, s));
     WZ_RUN(cudaStreamSynchronize(s));
@@ -236,12 +241,29 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     for (int j = 0; j < nrhs; ++j) any |= hst[j].active != 0;
     if (!any) break;
   }
-#undef WZ_RUN
-
-  if (pc) {
+  if (!pc) break;
+  {
     int rc = apply_op<double>(c, WZ_OP_M0INV, xs, x, nrhs, 0.0, A64);
     if (rc) return rc;
+    rc = true_residuals(c, b, x, nrhs, shift, rel.data());
+    if (rc) return rc;
   }
+  bool again = false;
+  for (int j = 0; j < nrhs; ++j) {
+    if (hst[j].status == WZ_OK && hst[j].bnorm2 > 0.0 && rel[j] > tol) {
+      const double f = 0.5 * tol / rel[j];
+      hst[j].tol2 *= f * f;
+      hst[j].active = 1;
+      hst[j].run = 1;
+      hst[j].ru = 0;
+      again = true;
+    }
+  }
+  if (!again) break;
+  WZ_RUN(cudaMemcpyAsync(st, hst, sizeof(RhsState) * nrhs, cudaMemcpyHostToDevice, s));
+  }
+#undef WZ_RUN
+
   SolveOut o;
   for (int j = 0; j < nrhs; ++j) {
     o.iterations = hst[j].iters > o.iterations ? hst[j].iters : o.iterations;
@@ -249,8 +271,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     o.reliable_updates += hst[j].ru_count;
     const bool ok = hst[j].active == 0 && hst[j].status == WZ_OK;
     o.converged += ok ? 1 : 0;
-    const double rel = hst[j].bnorm2 > 0 ? sqrt(hst[j].rtrue2 / hst[j].bnorm2) : 0.0;
-    o.max_true_residual = rel > o.max_true_residual ? rel : o.max_true_residual;
+    const double rj = pc ? rel[j] : (hst[j].bnorm2 > 0 ? sqrt(hst[j].rtrue2 / hst[j].bnorm2) : 0.0);
+    o.max_true_residual = rj > o.max_true_residual ? rj : o.max_true_residual;
   }
   *out = o;
   return o.converged == nrhs ? WZ_OK : WZ_NOT_CONVERGED;

@@ -42,6 +42,7 @@ struct RhsState {
   double bnorm2;   // |b|^2
   double rmax2;    // |r|^2 at the last reliable update
   double rtrue2;   // |b - A x|^2 at the last reliable update (FP64)
+  double tol2;     // stop when |b - A x|^2 <= tol2 |b|^2
   int run;         // iteration passes act on this RHS
   int ru;          // reliable update pending
   int active;      // not finished
@@ -218,7 +219,7 @@ __global__ void cg_init(const cplx<double>* b, cplx<R>* r, cplx<R>* x, long n_pe
 }
 
 // One warp per RHS.
-static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk) {
+static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk, double tol2) {
   RhsState* s = st + blockIdx.x;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
   if (threadIdx.x == 0) {
@@ -228,6 +229,7 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
     s->beta = 0.0;
     s->rmax2 = t;
     s->rtrue2 = t;
+    s->tol2 = tol2;
     s->iters = 0;
     s->ru_count = 0;
     s->ru = 0;
@@ -237,7 +239,7 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
   }
 }
 
-static __global__ void cg_scalar_iter(RhsState* st, const double* part, int nblk, double tol2, double delta2, int maxiter) {
+static __global__ void cg_scalar_iter(RhsState* st, const double* part, int nblk, double delta2, int maxiter) {
   RhsState* s = st + blockIdx.x;
   if (!s->run) return;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
@@ -246,14 +248,14 @@ static __global__ void cg_scalar_iter(RhsState* st, const double* part, int nblk
     s->beta = t / s->rr;
     s->rr_prev = s->rr;
     s->rr = t;
-    if (t <= delta2 * s->rmax2 || t <= tol2 * s->bnorm2 || s->iters >= maxiter) {
+    if (t <= delta2 * s->rmax2 || t <= s->tol2 * s->bnorm2 || s->iters >= maxiter) {
       s->ru = 1;
       s->run = 0;
     }
   }
 }
 
-static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, double tol2, int maxiter) {
+static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, int maxiter) {
   RhsState* s = st + blockIdx.x;
   if (!s->ru) return;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
@@ -261,7 +263,7 @@ static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, 
     s->ru = 0;
     s->ru_count += 1;
     s->rtrue2 = t;
-    if (t <= tol2 * s->bnorm2) {
+    if (t <= s->tol2 * s->bnorm2) {
       s->active = 0;
       s->run = 0;
       s->status = WZ_OK;

@@ -68,8 +68,13 @@ struct wz_ctx {
   wz::DevBuf ws_solver;   // solver vectors
   wz::DevBuf ws_red;      // reduction partials and per-RHS scalars
   wz::DevBuf ws_force;    // force / HMC fields
-  void* host_pinned = nullptr;  // small pinned block for scalar read-back
+  // small pinned block for scalar read-back: [0, WZ_PINNED_SCRATCH_OFFSET) holds
+  // the solver's per-RHS state, the rest is scratch for other reductions
+  void* host_pinned = nullptr;
 };
+
+#define WZ_PINNED_BYTES (256 * 1024)
+#define WZ_PINNED_SCRATCH_OFFSET (128 * 1024)
 
 namespace wz {
 

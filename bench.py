@@ -1,0 +1,326 @@
+"""Benchmark of the overlap-fermion hot path on GB300.
+
+Workload (precision workload): 16^4 lattice, a = r = M0 = 1, m = 0.05,
+g = 0.3, phi Gaussian sigma 0.5 (seed 0), 12 complex-Gaussian right-hand
+sides (seed 1).  One step = solve (M^dagger M) x = b for all 12 right-hand
+sides by the library's CG, FP32 iteration with FP64 reliable updates, to an
+FP64 true relative residual <= 1e-10.
+
+value = M^dagger M applies per second over the timed steps, with
+applies = sum over right-hand sides of the CG iterations (one FP32 M^dagger M
+each) plus the FP64 M^dagger M applies of the reliable updates.  The inputs
+are resident on the device; L2 is flushed (256 MB write) before every step.
+
+Extra keys: the same solve in FP64 throughout (the baseline the mixed path
+must beat), "e2e" through the C ABI with host buffers, a roofline of the
+dominant kernel from the library's event probe, the FP64 CPU oracle timed on
+a bounded sample, SM clocks sampled during the timed region, and the count of
+library kernels launched in the timed region.
+
+--impl reference times the FP64 CPU oracle (the plain definitions) on the
+host cores with the same metric.  Under torchrun every rank runs its own
+independent replica (the path does not shard a single lattice); rank 0
+prints one JSON line with the aggregate over ranks.
+"""
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1005_3276_gb300 import synth  # noqa: E402
+
+METRIC = "M^dag M applies/s and HMC traj/s at 16^4, mixed vs FP64 GPU @1e-10 residual"
+UNIT = "M^dag M applies/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="wz", choices=["wz", "reference"])
+    ap.add_argument("--probe", default="zt", help="kernel class for the roofline probe")
+    ap.add_argument("--probe-bytes", type=int, default=4)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_config(w):
+    return {
+        "workload": f"{w.name}: 16^4 lattice (T=Z=Y=X=16), m={w.m}, g={w.g}, phi Gaussian sigma {w.sigma}, "
+                    f"{w.nrhs} complex-Gaussian RHS, CG on M^dag M to {w.tol:g} FP64 true residual",
+        "lattice": "16^4",
+        "nrhs": w.nrhs,
+        "tol": w.tol,
+        "solver": "CG, FP32 iteration + FP64 reliable updates (delta 0.1)",
+        "l2": "flushed before every step (256 MB write); solver working set ~330 MB > L2",
+    }
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+
+def oracle_applies_per_s(w, seconds):
+    """FP64 oracle CG iterations (one M^dag M each) on RHS 0 for ~seconds."""
+    import oracle
+    P = oracle.Params(dims=w.dims, m=w.m, g=w.g)
+    phi = synth.scalar_field(w.dims, w.sigma, 0)
+    b = synth.spinor_rhs(1, w.dims, 1)[0]
+    A = lambda v: oracle.fftops.apply_MdagM(P, phi, v)  # noqa: E731
+    A(b)  # warm caches
+    t0 = time.perf_counter()
+    c0 = time.process_time()
+    n = 0
+    x = np.zeros_like(b)
+    r = b.copy()
+    p = r.copy()
+    rr = np.vdot(r, r).real
+    while time.perf_counter() - t0 < seconds:
+        Ap = A(p)
+        alpha = rr / np.vdot(p, Ap).real
+        x += alpha * p
+        r -= alpha * Ap
+        rr_new = np.vdot(r, r).real
+        p = r + (rr_new / rr) * p
+        rr = rr_new
+        n += 1
+    dt = time.perf_counter() - t0
+    oracle_applies_per_s.cores = max(1, round((time.process_time() - c0) / dt))
+    return n / dt, n, dt
+
+
+def cpu_threads():
+    """Threads the oracle sample actually kept busy: process CPU time / wall time."""
+    return getattr(oracle_applies_per_s, "cores", 1)
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    secs = max(2.0, min(20.0, 120.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        oracle_applies_per_s(w, secs / 4)
+    vals, total_n, total_t = [], 0, 0.0
+    for _ in range(args.steps):
+        v, n, dt = oracle_applies_per_s(w, secs)
+        vals.append(v)
+        total_n += n
+        total_t += dt
+    value = total_n / total_t
+    sample = f"FP64 oracle CG iterations on RHS 0 of {w.name}, {total_n} M^dag M applies in {total_t:.1f} s"
+    cores = cpu_threads()
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * total_t / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(w),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+
+def main():
+    args = parse()
+    w = synth.PRECISION_16
+    if args.impl == "reference":
+        run_reference(args, w)
+        return
+
+    import torch
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    from paper_1005_3276_gb300 import binding as wz
+
+    stream = torch.cuda.current_stream()
+    phi = synth.scalar_field(w.dims, w.sigma, 0)
+    b = synth.spinor_rhs(w.nrhs, w.dims, 1)
+    lat = wz.Lattice(w.dims, m=w.m, g=w.g, stream=stream.cuda_stream)
+    lat.set_phi(torch.from_numpy(phi).cuda())
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros_like(bd)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def solve(mixed=True):
+        rc, st, _ = lat.solve(bd, xd, tol=w.tol, mixed=mixed)
+        assert st["converged"] == w.nrhs and st["max_true_residual"] <= w.tol, st
+        return st["total_iterations"] + st["reliable_updates"], st
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = wz.wz_kernel_launches()
+    wz.wz_probe_begin(args.probe, args.probe_bytes)
+    total_ms, total_applies, stats = 0.0, 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n, st = solve()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        total_ms += e0.elapsed_time(e1)
+        total_applies += n
+        stats.append(st)
+    probe = wz.wz_probe_end()
+    launches = wz.wz_kernel_launches() - launches0
+    clk = clocks.stop()
+
+    # max time over ranks, sum of work over ranks
+    t_max, applies_all = total_ms, total_applies
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        a = torch.tensor([float(total_applies)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(a, op=dist.ReduceOp.SUM)
+        t_max, applies_all = float(t.item()), int(a.item())
+    value = applies_all / (t_max / 1000.0)
+
+    # FP64 throughout, same workload (one solve)
+    fp64 = None
+    if not args.no_fp64:
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n64, st64 = solve(mixed=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": n64 / (ms64 / 1000.0), "unit": UNIT, "ms_per_solve": ms64,
+                "iterations": st64["iterations"], "max_true_residual": st64["max_true_residual"],
+                "mixed_speedup_per_solve": ms64 / (total_ms / args.steps)}
+
+    # end to end through the C ABI with pinned host buffers
+    hb = torch.from_numpy(b).pin_memory()
+    hx = torch.zeros_like(hb).pin_memory()
+    e2e_t, e2e_n = 0.0, 0
+    for _ in range(0 if args.no_e2e else max(1, min(args.steps, 2))):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc, st, _ = lat.solve(hb, hx, tol=w.tol, mixed=True)
+        e2e_t += time.perf_counter() - t0
+        e2e_n += st["total_iterations"] + st["reliable_updates"]
+    e2e = {"value": e2e_n / e2e_t if e2e_t > 0 else None, "unit": UNIT, "h2d_bytes_per_step": int(hb.numel() * hb.element_size()),
+           "d2h_bytes_per_step": int(hx.numel() * hx.element_size())}
+
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = peaks.get("hbm_gbs")
+    peak_src = "measured" if peak else "fallback"
+    peak = peak or 6800.0
+    achieved = probe["bytes"] / (probe["total_ms"] / 1000.0) / 1e9 if probe["total_ms"] > 0 else None
+    roofline = {"bound": "hbm", "kernel": f"{args.probe} (FP{8 * args.probe_bytes})",
+                "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "peak_source": peak_src,
+                "traffic": None, "launches": probe["launches"],
+                "avg_launch_us": 1000.0 * probe["total_ms"] / max(1, probe["timed_launches"]),
+                "algorithmic_bytes_per_launch": probe["bytes"] / max(1, probe["launches"])}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, n, dt = oracle_applies_per_s(w, args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
+               "sample": f"FP64 oracle CG iterations on RHS 0 of {w.name}: {n} M^dag M applies in {dt:.1f} s"}
+
+    if rank == 0:
+        it = [s["iterations"] for s in stats]
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
+            "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
+                      "max_true_residual": max(s["max_true_residual"] for s in stats)},
+            "fp64": fp64, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "gpu_launches": int(launches),
+        }))
+    lat.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

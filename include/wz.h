@@ -125,6 +125,28 @@ typedef struct wz_solve_stats {
 int wz_solve(wz_ctx* ctx, const void* b, void* x, int nrhs, double shift, double tol, int maxiter,
              unsigned flags, wz_solve_stats* stats, double* resid);
 
+/* ---- measurement (not part of the method; the paper times whole solves) ----
+ * Process-wide count of kernels launched by the library so far. */
+unsigned long long wz_kernel_launches(void);
+
+/* Kernel probe.  wz_probe_begin arms a probe for one kernel class:
+ *   kind 0 zt pass, 1 apply xy pass, 2..4 CG passes P1/P3/P5, 5..6 reliable-update
+ *   passes; real_bytes 4 (FP32 kernels) or 8 (FP64 kernels).
+ * Until wz_probe_end, every launch of that class is bracketed by CUDA events
+ * on its stream (first 8192 launches) and each block that does work (is not
+ * gated off) adds the algorithmic bytes it moves -- the spinor, phi and
+ * table bytes it must read and write -- to a device counter.  wz_probe_end
+ * synchronises the device and returns the summed event time of the timed
+ * launches and the summed algorithmic bytes. */
+typedef struct wz_probe_result {
+  long launches;        /* launches of the class while armed */
+  long timed_launches;  /* launches bracketed by events */
+  double total_ms;      /* summed event time of the timed launches */
+  double bytes;         /* algorithmic bytes moved by the blocks that ran */
+} wz_probe_result;
+int wz_probe_begin(int kind, int real_bytes);
+int wz_probe_end(wz_probe_result* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,14 @@ class WzSolveStats(ctypes.Structure):
 WZ_SOLVE_MIXED, WZ_SOLVE_PC = 1, 2
 
 
+class WzProbeResult(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_long), ("timed_launches", ctypes.c_long),
+                ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
+
+
+PROBE_KINDS = {"zt": 0, "xy": 1, "cg_p1": 2, "cg_p3": 3, "cg_p5": 4, "ru_p1": 5, "ru_p5": 6}
+
+
 class WzError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"wz status {code}: {msg}")
@@ -62,6 +70,9 @@ def _load():
         "wz_apply": ([P, I, I, P, P, I, D], I),
         "wz_solve": ([P, P, P, I, D, D, I, ctypes.c_uint, ctypes.POINTER(WzSolveStats),
                       ctypes.POINTER(ctypes.c_double)], I),
+        "wz_kernel_launches": ([], ctypes.c_ulonglong),
+        "wz_probe_begin": ([I, I], I),
+        "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -73,7 +84,7 @@ def _load():
 LIB = _load()
 
 EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply",
-           "wz_solve")
+           "wz_solve", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
 def _is_torch(x):
@@ -161,6 +172,20 @@ def wz_solve(ctx, b, x, nrhs, shift=0.0, tol=1e-10, maxiter=100000, flags=WZ_SOL
     if rc not in (WZ_OK, WZ_NOT_CONVERGED) or (rc == WZ_NOT_CONVERGED and raise_on_nonconvergence):
         check(ctx, rc)
     return rc, st.as_dict(), (list(res)[:nrhs] if resid else None)
+
+
+def wz_kernel_launches():
+    return int(LIB.wz_kernel_launches())
+
+
+def wz_probe_begin(kind, real_bytes):
+    return check(None, LIB.wz_probe_begin(PROBE_KINDS.get(kind, kind), int(real_bytes)))
+
+
+def wz_probe_end():
+    r = WzProbeResult()
+    check(None, LIB.wz_probe_end(ctypes.byref(r)))
+    return {k: getattr(r, k) for k, _ in r._fields_}
 
 
 class Lattice:

@@ -12,6 +12,9 @@
 
 namespace wz {
 
+Probe g_probe;
+unsigned long long g_launches = 0;
+
 int set_error(wz_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
   return code;
@@ -150,6 +153,7 @@ static int build_tables(wz_ctx* c) {
   a.hdVf = c->t32.hdV;
   a.dVf = c->t32.dV;
   const int blocks = (int)((V + 255) / 256 < 1024 ? (V + 255) / 256 : 1024);
+  g_launches += 2;
   momentum_tables_kernel<<<blocks, 256, 0, c->stream>>>(a);
   WZ_CUDA_TRY(c, cudaGetLastError());
   axis_tables_kernel<<<1, 256, 0, c->stream>>>(c->T, c->Z, c->Y, c->X, c->t64.sinT, c->t32.sinT);
@@ -265,6 +269,7 @@ int wz_set_phi(wz_ctx* c, const void* phi) {
   if (!c || !phi) return set_error(c, WZ_EINVAL, "wz_set_phi: null pointer");
   const size_t n = sizeof(cplx<double>) * c->V;
   WZ_CUDA_TRY(c, cudaMemcpyAsync(c->phi64, phi, n, cudaMemcpyDefault, c->stream));
+  ++g_launches;
   phi_to_f32_kernel<<<(unsigned)((c->V + 255) / 256 < 2048 ? (c->V + 255) / 256 : 2048), 256, 0, c->stream>>>(
       c->phi64, c->phi32, c->V);
   WZ_CUDA_TRY(c, cudaGetLastError());
@@ -334,6 +339,49 @@ int wz_solve(wz_ctx* c, const void* b, void* x, int nrhs, double shift, double t
   }
   if (rc == WZ_NOT_CONVERGED) set_error(c, rc, "wz_solve: maxiter reached before tol");
   return rc;
+}
+
+unsigned long long wz_kernel_launches(void) { return g_launches; }
+
+int wz_probe_begin(int kind, int real_bytes) {
+  Probe& p = g_probe;
+  if (kind < PK_ZT || kind > PK_RU_P5 || (real_bytes != 4 && real_bytes != 8)) return WZ_EINVAL;
+  if (!p.d_blocks && cudaMalloc(&p.d_blocks, sizeof(unsigned long long)) != cudaSuccess) return WZ_ENOMEM;
+  if (p.ev.empty()) {
+    p.ev.resize(2 * 8192);
+    for (auto& e : p.ev)
+      if (cudaEventCreate(&e) != cudaSuccess) return WZ_ECUDA;
+  }
+  if (cudaMemset(p.d_blocks, 0, sizeof(unsigned long long)) != cudaSuccess) return WZ_ECUDA;
+  p.kind = kind;
+  p.real_bytes = real_bytes;
+  p.recorded = 0;
+  p.launches = 0;
+  p.bytes_per_block = 0.0;
+  p.active = 1;
+  return WZ_OK;
+}
+
+int wz_probe_end(wz_probe_result* out) {
+  Probe& p = g_probe;
+  if (!p.active) return WZ_EINVAL;
+  p.active = 0;
+  if (cudaDeviceSynchronize() != cudaSuccess) return WZ_ECUDA;
+  double ms = 0.0;
+  for (int i = 0; i < p.recorded; ++i) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p.ev[2 * i], p.ev[2 * i + 1]) != cudaSuccess) return WZ_ECUDA;
+    ms += t;
+  }
+  unsigned long long bytes = 0;
+  if (cudaMemcpy(&bytes, p.d_blocks, sizeof(bytes), cudaMemcpyDeviceToHost) != cudaSuccess) return WZ_ECUDA;
+  if (out) {
+    out->launches = p.launches;
+    out->timed_launches = p.recorded;
+    out->total_ms = ms;
+    out->bytes = (double)bytes;
+  }
+  return WZ_OK;
 }
 
 }  // extern "C"

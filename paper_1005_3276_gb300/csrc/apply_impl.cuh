@@ -8,6 +8,7 @@
 #pragma once
 #include "wz_ctx.h"
 #include "wz_kernels.cuh"
+#include "wz_probe.h"
 
 namespace wz {
 
@@ -33,8 +34,20 @@ static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
   }
   const int grid = (a.nplanes + S::PPC - 1) / S::PPC;
   if (grid == 0) return cudaSuccess;
-  xy_pass<R, L, MODE><<<grid, S::THREADS, smem, st>>>(a);
-  return cudaGetLastError();
+  // algorithmic bytes of one block: the spinor fields it reads and writes,
+  // plus phi where the site term needs it
+  using I = XYModeInfo<MODE>;
+  int fields = (I::inv ? 1 : 0) + (I::fwd ? 1 : 0) + (a.psi ? 1 : 0) + (a.psi2 ? 1 : 0) + (a.v_out ? 1 : 0);
+  const bool uses_phi = !(MODE == XY_FWD || MODE == XY_INV || MODE == XY_INV_ADD);
+  const double site = 4.0 * sizeof(cplx<R>) * fields + (uses_phi ? sizeof(cplx<R>) : 0);
+  const double blk_bytes = site * L * L * S::PPC;
+  return probed(PK_XY, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
+    XYArgs<R> b = a;
+    b.blk_count = cnt;
+    b.probe_inc = (unsigned long long)blk_bytes;
+    xy_pass<R, L, MODE><<<grid, S::THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  });
 }
 
 template <typename R, int L>
@@ -77,8 +90,16 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   }
   const long grid = (long)nrhs * a.ntiles;
   if (grid == 0) return cudaSuccess;
-  zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(a);
-  return cudaGetLastError();
+  // one block reads and writes C columns x NZ x NT sites of 4 spins and reads
+  // the momentum tables it needs (1 for Dslash, 2 for M0^-1)
+  const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));
+  return probed(PK_ZT, (int)sizeof(R), bytes, st, [&](unsigned long long* cnt) {
+    ZTArgs<R> b = a;
+    b.blk_count = cnt;
+    b.probe_inc = (unsigned long long)bytes;
+    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  });
 }
 
 template <typename R, int NZ, int NT>

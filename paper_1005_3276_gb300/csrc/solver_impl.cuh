@@ -26,8 +26,25 @@ static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st
     attr_done = true;
   }
   dim3 grid(a.nblk, nrhs);
-  xy_cg<R, LO, L, MODE, PC><<<grid, S::THREADS, smem, st>>>(a);
-  return cudaGetLastError();
+  // algorithmic bytes of one block (PPC planes of L x L sites, 4 spins)
+  const double f = 4.0 * sizeof(cplx<R>), lo = 4.0 * sizeof(cplx<LO>), ph = sizeof(cplx<R>);
+  double site = 0.0;
+  int kind = PK_CG_P1;
+  switch (MODE) {
+    case CG_P1: site = 4 * f; kind = PK_CG_P1; break;                 // r, p in; p, A out
+    case CG_P3: site = 4 * f + ph; kind = PK_CG_P3; break;            // A, p in; C, A out; phi
+    case CG_P5: site = 7 * f + (PC ? 0 : ph); kind = PK_CG_P5; break; // A, p, C, x, r in; x, r out
+    case RU_P1: site = 3 * f + 2 * lo; kind = PK_RU_P1; break;        // x_hi, x_lo in; x_hi, x_lo, A out
+    case RU_P5: site = 4 * f + lo + (PC ? 0 : ph); kind = PK_RU_P5; break;  // A, x_hi, C, b in; r out
+  }
+  const double blk_bytes = site * L * L * S::PPC;
+  return probed(kind, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
+    CGArgs<R, LO> b = a;
+    b.blk_count = cnt;
+    b.probe_inc = (unsigned long long)blk_bytes;
+    xy_cg<R, LO, L, MODE, PC><<<grid, S::THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  });
 }
 
 template <typename R, typename LO, int L, bool PC>
@@ -132,6 +149,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   }
 
   WZ_CUDA_TRY(c, cudaMemsetAsync(xs, 0, W.field64, s));
+  g_launches += 2;
   cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, n_per_rhs, partR, 64);
   WZ_CUDA_TRY(c, cudaGetLastError());
   cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol);
@@ -209,6 +227,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       a5.part_in = part3;
       a5.part_out = part5;
       WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, s));
+      ++g_launches;
       cg_scalar_iter<<<nrhs, 32, 0, s>>>(st, part5, nblk, delta2, maxiter);
       WZ_RUN(cudaGetLastError());
     }
@@ -233,6 +252,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     CGArgs<double, RI> r5 = ra;
     r5.part_out = partR;
     WZ_RUN(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, s));
+    ++g_launches;
     cg_scalar_ru<<<nrhs, 32, 0, s>>>(st, partR, nblk, maxiter);
     WZ_RUN(cudaGetLastError());
     WZ_RUN(cudaMemcpyAsync(hst, st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, s));

@@ -71,6 +71,8 @@ template <typename R, typename LO> struct CGArgs {
   int nblk;             // blocks per right-hand side
   int TZ;               // planes per right-hand side
   int gate_ru;          // 1: act on RHS with a pending reliable update; 0: on running RHS
+  unsigned long long* blk_count;  // probe: byte counter (may be null)
+  unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -117,6 +119,7 @@ xy_cg(CGArgs<R, LO> a) {
   if (!(a.gate_ru ? st->ru : st->run)) return;  // whole block, before any barrier
 
   const int tid = threadIdx.x;
+  if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
   const int pl_local = tid / S::TPP;
   const int w = (tid / 4) % L;
   const int s = tid & 3;

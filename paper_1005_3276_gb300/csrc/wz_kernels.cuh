@@ -76,6 +76,8 @@ template <typename R> struct XYArgs {
   R shift;
   int nplanes;           // nrhs * T * Z
   int TZ;                // planes per right-hand side
+  unsigned long long* blk_count;  // probe: byte counter (may be null)
+  unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
 
 // Threads per plane: 4 * L (one per (line, spin)); PPC planes per block, the
@@ -147,6 +149,7 @@ xy_pass(XYArgs<R> a) {
   const bool live = plane < a.nplanes;
   cplx<R>* P = sm + pl_local * S::PLANE;
   const long base = plane * (long)(L * L) * 4;  // complex offset of the plane
+  if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
 
   cplx<R> v[L];
 
@@ -244,6 +247,8 @@ template <typename R> struct ZTArgs {
   int X, XY;
   const int* gate;     // optional per-RHS run flag: block returns if gate[rhs * gate_stride] == 0
   int gate_stride;
+  unsigned long long* blk_count;  // probe: byte counter (may be null)
+  unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
 
 // Columns per block: 256 B contiguous per (z, t) row for short lines, fewer
@@ -274,6 +279,7 @@ zt_pass(ZTArgs<R> a) {
   const int q = tid / (4 * C);  // t in the z-phase, z in the t-phase
   const int rhs = blockIdx.x / a.ntiles;
   if (a.gate && !a.gate[(long)rhs * a.gate_stride]) return;  // whole block, before any barrier
+  if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
   const int col_raw = (blockIdx.x % a.ntiles) * C + c;  // (y, x) column = y * X + x
   // the last tile may be ragged (X * Y not a multiple of C): lanes past the
   // end keep computing on zeros so that every warp stays whole for the

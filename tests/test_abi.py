@@ -15,7 +15,7 @@ def declared_symbols():
     for fn in os.listdir(os.path.join(ROOT, "include")):
         if fn.endswith(".h"):
             src = open(os.path.join(ROOT, "include", fn)).read()
-            names |= set(re.findall(r"^\s*(?:int|const char\*|void)\s+\*?(wz_\w+)\s*\(", src, re.M))
+            names |= set(re.findall(r"^(?!typedef)[A-Za-z_][\w \*]*?\b(wz_\w+)\s*\(", src, re.M))
     return sorted(names)
 
 

@@ -150,7 +150,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
 
   WZ_CUDA_TRY(c, cudaMemsetAsync(xs, 0, W.field64, s));
   g_launches += 2;
-  cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, n_per_rhs, partR, 64);
+  cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, p, n_per_rhs, partR, 64);
   WZ_CUDA_TRY(c, cudaGetLastError());
   cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol);
   WZ_CUDA_TRY(c, cudaGetLastError());

@@ -157,7 +157,8 @@ xy_cg(CGArgs<R, LO> a) {
     for (int y = 0; y < L; ++y) {
       const long e = (site0 + y * L) * 4 + s;
       if constexpr (MODE == CG_P1) {
-        const cplx<R> pv = a.r[e] + beta * a.p[e];
+        // beta == 0 (first step): p = r without reading the previous p
+        const cplx<R> pv = beta != R(0) ? a.r[e] + beta * a.p[e] : a.r[e];
         a.p[e] = pv;
         v[y] = pv;
       } else if constexpr (MODE == CG_P3) {
@@ -204,9 +205,10 @@ xy_cg(CGArgs<R, LO> a) {
   }
 }
 
-// r = (R) b, x = 0, partial |b|^2 (FP64).  Grid (nblk, nrhs), one thread per complex.
+// r = (R) b, x = p = 0, partial |b|^2 (FP64).  Grid (nblk, nrhs).
 template <typename R>
-__global__ void cg_init(const cplx<double>* b, cplx<R>* r, cplx<R>* x, long n_per_rhs, double* part, int nblk) {
+__global__ void cg_init(const cplx<double>* b, cplx<R>* r, cplx<R>* x, cplx<R>* p, long n_per_rhs, double* part,
+                        int nblk) {
   __shared__ double red[33];
   const int rhs = blockIdx.y;
   double t = 0.0;
@@ -215,6 +217,7 @@ __global__ void cg_init(const cplx<double>* b, cplx<R>* r, cplx<R>* x, long n_pe
     const cplx<double> bv = b[e];
     r[e] = cplx<R>{(R)bv.x, (R)bv.y};
     x[e] = cplx<R>{R(0), R(0)};
+    p[e] = cplx<R>{R(0), R(0)};
     t += bv.x * bv.x + bv.y * bv.y;
   }
   t = block_sum(t, red);

@@ -129,3 +129,16 @@ def test_precision_workload_16(wz, mixed):
     for k in (0, w.nrhs - 1):
         assert ocg.true_residual(P, phi, b[k], xs[k]) <= TOL
     print(f"16^4 mixed={mixed}: {st}")
+
+
+def test_workspace_reuse_across_precisions(wz, small):
+    """A mixed solve after an FP64 solve on the same context reuses the
+    workspace with another layout; nothing of the old contents may leak in."""
+    w, P, phi, b, _, _ = small
+    lat = wz.Lattice(w.dims, m=w.m, g=w.g)
+    lat.set_phi(phi)
+    bd = torch.from_numpy(b).cuda()
+    x = torch.zeros_like(bd)
+    for mixed in (False, True, False, True):
+        lat.solve(bd, x, tol=TOL, mixed=mixed)
+        assert oracle_residual(P, phi, b, x.cpu().numpy()) <= TOL

@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wz", choices=["wz", "reference"])
-    ap.add_argument("--probe", default="zt", help="kernel class for the roofline probe")
+    ap.add_argument("--probe", default="cg_p5", help="kernel class for the roofline probe (the dominant kernel)")
     ap.add_argument("--probe-bytes", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")

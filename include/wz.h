@@ -125,6 +125,22 @@ typedef struct wz_solve_stats {
 int wz_solve(wz_ctx* ctx, const void* b, void* x, int nrhs, double shift, double tol, int maxiter,
              unsigned flags, wz_solve_stats* stats, double* resid);
 
+/* (M^dagger M + shift) psi like wz_apply(WZ_OP_MDAGM), without allocating.
+ * The paper has no counterpart: this serves callers that cannot allocate
+ * device memory at call time (all memory handed to their own pool, a loop in
+ * which a possibly synchronising cudaMalloc is not acceptable, or code that
+ * must not fail half-way with an out-of-memory error).  The pass
+ * intermediates live in a file-scope device array of 32 MiB that every GPU
+ * loading the library holds until exit; a call needing more (2 fields of
+ * nrhs x V x 4 complex: e.g. at 16^4 up to 2 RHS in C128, 4 in C64) returns
+ * WZ_EINVAL with a message.  in and out are device pointers of dtype on the
+ * context's device, which must be current (WZ_EINVAL otherwise); they may
+ * alias.  The first call on a device looks up the array's device address
+ * (and may load the library's device code there): make it during set-up,
+ * before any stream capture.  All calls share the array; calls that overlap
+ * on the GPU race on it.  Asynchronous on the context stream. */
+int wz_apply_mdagm_noalloc(wz_ctx* ctx, int dtype, const void* in, void* out, int nrhs, double shift);
+
 /* ---- measurement (not part of the method; the paper times whole solves) ----
  * Process-wide count of kernels launched by the library so far. */
 unsigned long long wz_kernel_launches(void);

@@ -70,6 +70,7 @@ def _load():
         "wz_apply": ([P, I, I, P, P, I, D], I),
         "wz_solve": ([P, P, P, I, D, D, I, ctypes.c_uint, ctypes.POINTER(WzSolveStats),
                       ctypes.POINTER(ctypes.c_double)], I),
+        "wz_apply_mdagm_noalloc": ([P, I, P, P, I, D], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
         "wz_probe_begin": ([I, I], I),
         "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
@@ -84,7 +85,7 @@ def _load():
 LIB = _load()
 
 EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply",
-           "wz_solve", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
+           "wz_solve", "wz_apply_mdagm_noalloc", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
 def _is_torch(x):
@@ -172,6 +173,13 @@ def wz_solve(ctx, b, x, nrhs, shift=0.0, tol=1e-10, maxiter=100000, flags=WZ_SOL
     if rc not in (WZ_OK, WZ_NOT_CONVERGED) or (rc == WZ_NOT_CONVERGED and raise_on_nonconvergence):
         check(ctx, rc)
     return rc, st.as_dict(), (list(res)[:nrhs] if resid else None)
+
+
+def wz_apply_mdagm_noalloc(ctx, inp, out, nrhs, shift=0.0):
+    """(M^dag M + shift) inp with the static device scratch (no allocation)."""
+    pin, dt = field_ptr(inp)
+    pout, _ = field_ptr(out, dt)
+    return check(ctx, LIB.wz_apply_mdagm_noalloc(ctx, dt, pin, pout, int(nrhs), float(shift)))
 
 
 def wz_kernel_launches():

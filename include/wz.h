@@ -125,6 +125,66 @@ typedef struct wz_solve_stats {
 int wz_solve(wz_ctx* ctx, const void* b, void* x, int nrhs, double shift, double tol, int maxiter,
              unsigned flags, wz_solve_stats* stats, double* resid);
 
+/* ---- forces, actions, molecular dynamics, HMC (Eq. acws; Sec. 7.2) ----
+ *
+ * Bosonic action S_B = sum_x [2 phi^* (D2 phi) + W'^* (1 - D2/2) W'], W' = m phi + g phi^2,
+ * scalars periodic (Eq. acws).  Pseudofermion action with one pole (Eq. jkjk with
+ * alpha = 1, beta = 0): S_pf = sum_k eta_k^dag (M^dag M)^-1 eta_k.  Forces are
+ * G = dS/dphi_R + i dS/dphi_I per site (complex128 [T][Z][Y][X]):
+ *   G_B  = 4 (D2 phi) + 2 conj(m + 2 g phi) ((1 - D2/2) W')
+ *   G_pf = -2 Re[Z^dag dM/dphi_R X] - 2i Re[Z^dag dM/dphi_I X], X = (M^dag M)^-1 eta, Z = M X
+ * phi is the context's field (wz_set_phi / wz_get_phi). */
+enum wz_force_parts { WZ_FORCE_FERMION = 1, WZ_FORCE_BOSON = 2 };
+enum wz_hmc_flags {
+  WZ_HMC_FP64_SOLVES = 1,    /* FP64 CG in the force (default: mixed FP32/FP64) */
+  WZ_HMC_NO_METROPOLIS = 2   /* keep the end of the molecular dynamics (tests) */
+};
+
+typedef struct wz_hmc_params {
+  double tau;              /* trajectory length */
+  int nsteps;              /* integration steps */
+  int integrator;          /* 0: leapfrog; 1: Omelyan 2MN, lambda = 0.1931833275037836 */
+  int npf;                 /* pseudofermions (one CG right-hand side each) */
+  double tol;              /* CG true relative residual of every force solve */
+  int maxiter;             /* per solve (<= 0: 100000) */
+  unsigned flags;          /* wz_hmc_flags */
+  unsigned long long seed; /* Philox4x32-10 key (Salmon et al. SC'11) */
+  unsigned int traj_index; /* counter word: trajectory number */
+} wz_hmc_params;
+
+typedef struct wz_traj_stats {
+  double H0, H1, dH, u;    /* Hamiltonians (FP64), dH = H1 - H0, Metropolis uniform */
+  int accept;
+  int force_evals;
+  long long cg_iterations; /* inner CG iterations summed over all solves and RHS */
+  int reliable_updates;
+  double seconds;
+} wz_traj_stats;
+
+/* Copy the context's phi (complex128, host or device pointer). */
+int wz_get_phi(wz_ctx* ctx, void* phi);
+
+/* grad = dS/dphi (complex128 [T][Z][Y][X], host or device) of S = S_B and/or
+ * S_pf (parts = wz_force_parts) at the context's phi; eta: npf complex128
+ * pseudofermion fields (host or device).  S_B and S_pf (may be NULL) receive
+ * the actions.  The solves use mixed precision to FP64 true residual tol.
+ * Synchronous.  WZ_NOT_CONVERGED if a solve hit its iteration cap. */
+int wz_force(wz_ctx* ctx, const void* eta, int npf, double tol, unsigned parts, void* grad, double* S_B,
+             double* S_pf, wz_solve_stats* stats);
+
+/* Molecular dynamics of length h->tau in h->nsteps steps from (phi, pi) with
+ * fixed pseudofermions eta (npf, complex128): phi (context) and pi (complex128
+ * [T][Z][Y][X], host or device, updated in place) evolve by d phi = pi,
+ * d pi = -G.  Synchronous. */
+int wz_md_integrate(wz_ctx* ctx, void* pi, const void* eta, int npf, const wz_hmc_params* h, wz_traj_stats* st);
+
+/* One HMC trajectory on the context's phi: pi ~ N(0,1) per real component and
+ * R_k ~ exp(-|R|^2) drawn on the device from Philox4x32-10 (key = seed,
+ * counter = (site, draw, stream, traj_index)), eta_k = M^dag R_k,
+ * H = |pi|^2/2 + S_B + S_pf in FP64, molecular dynamics, Metropolis on the
+ * device with a Philox uniform; on rejection phi is restored.  Synchronous. */
+int wz_trajectory(wz_ctx* ctx, const wz_hmc_params* h, wz_traj_stats* st);
+
 /* (M^dagger M + shift) psi like wz_apply(WZ_OP_MDAGM), without allocating.
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory at call time (all memory handed to their own pool, a loop in

@@ -47,6 +47,26 @@ class WzProbeResult(ctypes.Structure):
                 ("total_ms", ctypes.c_double), ("bytes", ctypes.c_double)]
 
 
+class WzHmcParams(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double), ("nsteps", ctypes.c_int), ("integrator", ctypes.c_int),
+                ("npf", ctypes.c_int), ("tol", ctypes.c_double), ("maxiter", ctypes.c_int),
+                ("flags", ctypes.c_uint), ("seed", ctypes.c_ulonglong), ("traj_index", ctypes.c_uint)]
+
+
+class WzTrajStats(ctypes.Structure):
+    _fields_ = [("H0", ctypes.c_double), ("H1", ctypes.c_double), ("dH", ctypes.c_double),
+                ("u", ctypes.c_double), ("accept", ctypes.c_int), ("force_evals", ctypes.c_int),
+                ("cg_iterations", ctypes.c_longlong), ("reliable_updates", ctypes.c_int),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+WZ_FORCE_FERMION, WZ_FORCE_BOSON = 1, 2
+WZ_HMC_FP64_SOLVES, WZ_HMC_NO_METROPOLIS = 1, 2
+INTEGRATORS = {"leapfrog": 0, "omelyan": 1}
+
 PROBE_KINDS = {"zt": 0, "xy": 1, "cg_p1": 2, "cg_p3": 3, "cg_p5": 4, "ru_p1": 5, "ru_p5": 6}
 
 
@@ -71,6 +91,11 @@ def _load():
         "wz_solve": ([P, P, P, I, D, D, I, ctypes.c_uint, ctypes.POINTER(WzSolveStats),
                       ctypes.POINTER(ctypes.c_double)], I),
         "wz_apply_mdagm_noalloc": ([P, I, P, P, I, D], I),
+        "wz_get_phi": ([P, P], I),
+        "wz_force": ([P, P, I, D, ctypes.c_uint, P, ctypes.POINTER(D), ctypes.POINTER(D),
+                      ctypes.POINTER(WzSolveStats)], I),
+        "wz_md_integrate": ([P, P, P, I, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
+        "wz_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
         "wz_probe_begin": ([I, I], I),
         "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
@@ -85,7 +110,8 @@ def _load():
 LIB = _load()
 
 EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply",
-           "wz_solve", "wz_apply_mdagm_noalloc", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
+           "wz_solve", "wz_apply_mdagm_noalloc", "wz_get_phi", "wz_force", "wz_md_integrate",
+           "wz_trajectory", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
 def _is_torch(x):
@@ -182,6 +208,41 @@ def wz_apply_mdagm_noalloc(ctx, inp, out, nrhs, shift=0.0):
     return check(ctx, LIB.wz_apply_mdagm_noalloc(ctx, dt, pin, pout, int(nrhs), float(shift)))
 
 
+def wz_get_phi(ctx, phi):
+    ptr, dt = field_ptr(phi, WZ_C128)
+    return check(ctx, LIB.wz_get_phi(ctx, ptr))
+
+
+def wz_force(ctx, eta, npf, grad, tol=1e-10, parts=WZ_FORCE_FERMION | WZ_FORCE_BOSON):
+    """grad <- dS/dphi; returns (S_B, S_pf, solve stats)."""
+    pe = field_ptr(eta, WZ_C128)[0] if npf > 0 else ctypes.c_void_p(0)
+    pg, _ = field_ptr(grad, WZ_C128)
+    sb, spf, st = ctypes.c_double(), ctypes.c_double(), WzSolveStats()
+    check(ctx, LIB.wz_force(ctx, pe, int(npf), float(tol), int(parts), pg, ctypes.byref(sb),
+                            ctypes.byref(spf), ctypes.byref(st)))
+    return sb.value, spf.value, st.as_dict()
+
+
+def hmc_params(tau=1.0, nsteps=10, integrator="leapfrog", npf=1, tol=1e-10, maxiter=0, flags=0, seed=0,
+               traj_index=0):
+    return WzHmcParams(float(tau), int(nsteps), INTEGRATORS.get(integrator, integrator), int(npf), float(tol),
+                       int(maxiter), int(flags), int(seed), int(traj_index))
+
+
+def wz_md_integrate(ctx, pi, eta, npf, params):
+    pp, _ = field_ptr(pi, WZ_C128)
+    pe = field_ptr(eta, WZ_C128)[0] if npf > 0 else ctypes.c_void_p(0)
+    st = WzTrajStats()
+    check(ctx, LIB.wz_md_integrate(ctx, pp, pe, int(npf), ctypes.byref(params), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def wz_trajectory(ctx, params):
+    st = WzTrajStats()
+    check(ctx, LIB.wz_trajectory(ctx, ctypes.byref(params), ctypes.byref(st)))
+    return st.as_dict()
+
+
 def wz_kernel_launches():
     return int(LIB.wz_kernel_launches())
 
@@ -234,6 +295,20 @@ class Lattice:
         flags = (WZ_SOLVE_MIXED if mixed else 0) | (WZ_SOLVE_PC if pc else 0)
         return wz_solve(self.ctx, b, x, self._nrhs(b), shift, tol, maxiter, flags, resid,
                         raise_on_nonconvergence)
+
+    def get_phi(self, phi):
+        return wz_get_phi(self.ctx, phi)
+
+    def force(self, eta, grad, tol=1e-10, parts=WZ_FORCE_FERMION | WZ_FORCE_BOSON):
+        npf = 0 if eta is None else self._nrhs(eta)
+        return wz_force(self.ctx, eta, npf, grad, tol, parts)
+
+    def md_integrate(self, pi, eta, **kw):
+        npf = 0 if eta is None else self._nrhs(eta)
+        return wz_md_integrate(self.ctx, pi, eta, npf, hmc_params(npf=npf, **kw))
+
+    def trajectory(self, **kw):
+        return wz_trajectory(self.ctx, hmc_params(**kw))
 
     def apply(self, op, inp, out, nrhs=None, shift=0.0):
         if nrhs is None:

@@ -60,8 +60,8 @@ bool zt_supported(int nz, int nt) {
 struct TableArgs {
   int T, Z, Y, X;
   double r, M0, m2, invV;
-  double *hV, *hdV, *dV;
-  float *hVf, *hdVf, *dVf;
+  double *hV, *hdV, *dV, *d2sV, *ksV;
+  float *hVf, *hdVf, *dVf, *d2sVf, *ksVf;
 };
 
 __global__ void momentum_tables_kernel(TableArgs a) {
@@ -90,6 +90,22 @@ __global__ void momentum_tables_kernel(TableArgs a) {
     a.hVf[i] = (float)a.hV[i];
     a.hdVf[i] = (float)a.hdV[i];
     a.dVf[i] = (float)a.dV[i];
+    // scalar symbols on the periodic grid (p_t = 2 pi nt / T): D2 = 1 - b/omega,
+    // K = 1 - D2/2 (Eq. acws); at the zone corners sum sin^2 = 0 and omega = |b|
+    double s2p = 0.0, wp = 0.0;
+    for (int mu = 0; mu < 4; ++mu) {
+      double sn, cs;
+      sincospi(mu == 0 ? 2.0 * nt / a.T : ang[mu], &sn, &cs);
+      s2p += sn * sn;
+      wp += 1.0 - cs;
+    }
+    const double bp = a.M0 - a.r * wp;
+    const double op = sqrt(bp * bp + s2p);
+    const double D2 = op > 0.0 ? 1.0 - bp / op : 1.0;
+    a.d2sV[i] = D2 * a.invV;
+    a.ksV[i] = (1.0 - 0.5 * D2) * a.invV;
+    a.d2sVf[i] = (float)a.d2sV[i];
+    a.ksVf[i] = (float)a.ksV[i];
   }
 }
 
@@ -120,7 +136,9 @@ template <typename R> static void carve(Tables<R>& t, R* base, long V, int T, in
   t.hV = base;
   t.hdV = base + V;
   t.dV = base + 2 * V;
-  R* ax = base + 3 * V;
+  t.d2sV = base + 3 * V;
+  t.ksV = base + 4 * V;
+  R* ax = base + 5 * V;
   t.sinT = ax;
   t.sinZ = ax + T;
   t.sinY = ax + T + Z;
@@ -132,7 +150,7 @@ template <typename R> static void carve(Tables<R>& t, R* base, long V, int T, in
 static int build_tables(wz_ctx* c) {
   const long V = c->V;
   const long naxis = 3L * c->T + c->Z + c->Y + c->X;
-  const long n = 3 * V + naxis;
+  const long n = 5 * V + naxis;
   WZ_CUDA_TRY(c, cudaMalloc(&c->t64.block, n * sizeof(double)));
   WZ_CUDA_TRY(c, cudaMalloc(&c->t32.block, n * sizeof(float)));
   carve(c->t64, (double*)c->t64.block, V, c->T, c->Z, c->Y, c->X);
@@ -149,9 +167,13 @@ static int build_tables(wz_ctx* c) {
   a.hV = c->t64.hV;
   a.hdV = c->t64.hdV;
   a.dV = c->t64.dV;
+  a.d2sV = c->t64.d2sV;
+  a.ksV = c->t64.ksV;
   a.hVf = c->t32.hV;
   a.hdVf = c->t32.hdV;
   a.dVf = c->t32.dV;
+  a.d2sVf = c->t32.d2sV;
+  a.ksVf = c->t32.ksV;
   const int blocks = (int)((V + 255) / 256 < 1024 ? (V + 255) / 256 : 1024);
   g_launches += 2;
   momentum_tables_kernel<<<blocks, 256, 0, c->stream>>>(a);

@@ -92,7 +92,7 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   if (grid == 0) return cudaSuccess;
   // one block reads and writes C columns x NZ x NT sites of 4 spins and reads
   // the momentum tables it needs (1 for Dslash, 2 for M0^-1)
-  const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));
+  const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));  // ZT_SCALAR: 2 tables too
   return probed(PK_ZT, (int)sizeof(R), bytes, st, [&](unsigned long long* cnt) {
     ZTArgs<R> b = a;
     b.blk_count = cnt;
@@ -108,6 +108,9 @@ static cudaError_t launch_zt_p(int mul, const ZTArgs<R>& a, int nrhs, cudaStream
     case ZT_DSLASH: return launch_zt_t<R, NZ, NT, ZT_DSLASH>(a, nrhs, st);
     case ZT_M0INV: return launch_zt_t<R, NZ, NT, ZT_M0INV>(a, nrhs, st);
     case ZT_M0INV_DAG: return launch_zt_t<R, NZ, NT, ZT_M0INV_DAG>(a, nrhs, st);
+    case ZT_SCALAR:
+      if constexpr (sizeof(R) == 8) return launch_zt_t<R, NZ, NT, ZT_SCALAR>(a, nrhs, st);
+      break;
   }
   return cudaErrorInvalidValue;
 }
@@ -150,6 +153,8 @@ template <typename R> static ZTArgs<R> zt_args(const wz_ctx* c, R sign) {
   a.hV = t.hV;
   a.hdV = t.hdV;
   a.dV = t.dV;
+  a.d2sV = t.d2sV;
+  a.ksV = t.ksV;
   a.sinT = t.sinT;
   a.sinZ = t.sinZ;
   a.sinY = t.sinY;

@@ -18,6 +18,8 @@ template <typename R> struct Tables {
   R* hV = nullptr;
   R* hdV = nullptr;
   R* dV = nullptr;
+  R* d2sV = nullptr;  // scalar D2(p)/V, periodic grid (Eq. acws)
+  R* ksV = nullptr;   // scalar K(p)/V = (1 - D2/2)/V
   R* sinT = nullptr;
   R* sinZ = nullptr;
   R* sinY = nullptr;

@@ -1,0 +1,287 @@
+// Forces, actions and HMC field updates (Eq. acws, Secs. 7.2 and 7.4).
+//
+//   S_B   = sum_x [ 2 phi^* (D2 phi) + W'^* (K W') ],  W' = m phi + g phi^2,
+//           K = 1 - D2/2, scalars periodic in every direction          (Eq. acws)
+//   S_pf  = sum_k eta_k^dag (M^dag M)^-1 eta_k   (single pole of Eq. jkjk)
+//   G     = dS/dphi_R + i dS/dphi_I
+//   G_B   = 4 (D2 phi) + 2 conj(m + 2 g phi) (K W')
+//   G_pf  = -2 Re[Z^dag dM/dphi_R X] - 2i Re[Z^dag dM/dphi_I X],  X = (M^dag M)^-1 eta, Z = M X
+//           dM/dphi_R = c g P_+ + c g^* P_-,  dM/dphi_I = i c g P_+ - i c g^* P_-
+//
+// Kernels (FP64; all site-local work is fused into the last xy pass):
+//   xy_force      inverse xy of F(M X without the site term), Z = . + Y X, the
+//                 site contraction above for one pseudofermion per plane -> G_k
+//   xy_boson_fwd  forward xy of the packed scalar field [phi, W', 0, 0]
+//   xy_boson_inv  inverse xy of [D2 phi, K W', ., .] (zt pass ZT_SCALAR), G_B,
+//                 + sum_k G_k in fixed order, partial S_B per block
+// plus Philox draws and the field updates of the molecular dynamics.
+#pragma once
+#include "wz_cg.cuh"
+
+namespace wz {
+
+template <typename R> struct ForceArgs {
+  const cplx<R>* A;       // momentum intermediate (input of the inverse passes)
+  cplx<R>* A_out;         // xy_boson_fwd output
+  const cplx<R>* X;       // xy_force: solutions X_k [npf][T][Z][Y][X][4]
+  cplx<R>* Gk;            // xy_force: per-pseudofermion forces [npf][V]
+  const cplx<R>* Gk_in;   // xy_boson_inv: forces to add, [npf][V] (may be null)
+  int npf;
+  cplx<R>* G;             // xy_boson_inv: total force [V] (may be null)
+  double* part;           // xy_boson_inv: block partials of S_B
+  const cplx<R>* phi;
+  SiteCoef<R> k;          // m, c g
+  R g_re, g_im;           // g (superpotential W' = m phi + g phi^2)
+  int TZ;
+  int nblk;
+  long V;
+};
+
+template <typename R>
+__device__ __forceinline__ R quad_sum(R v) {
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  return v;
+}
+
+// grid (nblk, npf); one pseudofermion per grid row
+template <int L>
+__global__ void __launch_bounds__(XYShape<L>::THREADS) xy_force(ForceArgs<double> a) {
+  using R = double;
+  using S = XYShape<L>;
+  using H = XYPhase<R, L>;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int k = blockIdx.y;
+  const int tid = threadIdx.x, pl_local = tid / S::TPP, w = (tid / 4) % L, s = tid & 3;
+  const int plane_in = blockIdx.x * S::PPC + pl_local;
+  const bool live = plane_in < a.TZ;
+  const long plane = (long)k * a.TZ + plane_in;
+  cplx<R>* P = sm + pl_local * S::PLANE;
+  const long base = plane * (long)(L * L) * 4;
+  cplx<R> v[L];
+  if (live) H::inv_x(a.A + base, P, w, s, v);
+  __syncthreads();
+  if (live) H::inv_y(P, w, s, v);
+  const cplx<R> cg{a.k.cg_re, a.k.cg_im};
+  // chirality weight: spins 2,3 (P_+) carry c g, spins 0,1 (P_-) carry c g^*
+  const cplx<R> wgt = s >= 2 ? cg : conj(cg);
+  const R sgn = s >= 2 ? R(1) : R(-1);
+#pragma unroll
+  for (int y = 0; y < L; ++y) {
+    R dr = 0, di = 0;
+    const long site = (long)plane_in * (L * L) + y * L + w;  // within one field
+    if (live) {
+      const long e = (plane * (long)(L * L) + y * L + w) * 4 + s;
+      const cplx<R> x = a.X[e];
+      const cplx<R> f = a.phi[site];
+      const cplx<R> z = v[y] + site_coef<R, false, true>(a.k, f, s) * x;  // Z = M X
+      const cplx<R> zx = conj(z) * x;
+      const cplx<R> t = wgt * zx;
+      dr = -R(2) * t.x;        // -2 Re[w Z^* X]
+      di = R(2) * sgn * t.y;   // -2 Re[+-i w Z^* X] = +-2 Im[w Z^* X]
+    }
+    dr = quad_sum(dr);
+    di = quad_sum(di);
+    if (live && s == 0) a.Gk[(long)k * a.V + site] = cplx<R>{dr, di};
+  }
+}
+
+// 1D grid over the T*Z planes of the packed scalar field
+template <int L>
+__global__ void __launch_bounds__(XYShape<L>::THREADS) xy_boson_fwd(ForceArgs<double> a) {
+  using R = double;
+  using S = XYShape<L>;
+  using H = XYPhase<R, L>;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
+  const int tid = threadIdx.x, pl_local = tid / S::TPP, w = (tid / 4) % L, s = tid & 3;
+  const int plane_in = blockIdx.x * S::PPC + pl_local;
+  const bool live = plane_in < a.TZ;
+  cplx<R>* P = sm + pl_local * S::PLANE;
+  const long base = (long)plane_in * (L * L) * 4;
+  cplx<R> v[L];
+  if (live) {
+#pragma unroll
+    for (int y = 0; y < L; ++y) {
+      const cplx<R> f = a.phi[(long)plane_in * (L * L) + y * L + w];
+      if (s == 0) v[y] = f;
+      else if (s == 1) v[y] = cplx<R>{a.k.m_re, a.k.m_im} * f + cplx<R>{a.g_re, a.g_im} * (f * f);
+      else v[y] = cplx<R>{0, 0};
+    }
+    H::fwd_y(v, P, w, s);
+  }
+  __syncthreads();
+  if (live) H::fwd_x(P, a.A_out + base, w, s, v);
+}
+
+template <int L>
+__global__ void __launch_bounds__(XYShape<L>::THREADS) xy_boson_inv(ForceArgs<double> a) {
+  using R = double;
+  using S = XYShape<L>;
+  using H = XYPhase<R, L>;
+  extern __shared__ unsigned char smem_raw[];
+  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
+  double* red = reinterpret_cast<double*>(sm + S::PLANE * S::PPC);
+  const int tid = threadIdx.x, pl_local = tid / S::TPP, w = (tid / 4) % L, s = tid & 3;
+  const int lane = tid & 31;
+  const int plane_in = blockIdx.x * S::PPC + pl_local;
+  const bool live = plane_in < a.TZ;
+  cplx<R>* P = sm + pl_local * S::PLANE;
+  const long base = (long)plane_in * (L * L) * 4;
+  cplx<R> v[L];
+  if (live) H::inv_x(a.A + base, P, w, s, v);
+  __syncthreads();
+  if (live) H::inv_y(P, w, s, v);
+  double part = 0.0;
+  const cplx<R> m{a.k.m_re, a.k.m_im}, g{a.g_re, a.g_im};
+#pragma unroll
+  for (int y = 0; y < L; ++y) {
+    cplx<R> d2, kw;  // (D2 phi) from spin slot 0, (K W') from slot 1 of this site
+    d2.x = __shfl_sync(0xffffffffu, v[y].x, lane & ~3);
+    d2.y = __shfl_sync(0xffffffffu, v[y].y, lane & ~3);
+    kw.x = __shfl_sync(0xffffffffu, v[y].x, (lane & ~3) | 1);
+    kw.y = __shfl_sync(0xffffffffu, v[y].y, (lane & ~3) | 1);
+    if (live && s == 0) {
+      const long site = (long)plane_in * (L * L) + y * L + w;
+      const cplx<R> f = a.phi[site];
+      const cplx<R> W = m * f + g * (f * f);
+      const cplx<R> dW = m + R(2) * (g * f);  // W'' = m + 2 g phi
+      cplx<R> G = R(4) * d2 + R(2) * (conj(dW) * kw);
+      for (int j = 0; j < a.npf; ++j) G = G + a.Gk_in[(long)j * a.V + site];
+      if (a.G) a.G[site] = G;
+      part += R(2) * re_conj_mul(d2, f) + re_conj_mul(kw, W);  // 2 Re[phi^* D2 phi] + Re[W'^* K W']
+    }
+  }
+  const double t = block_sum(part, red);
+  if (tid == 0) a.part[blockIdx.x] = t;
+}
+
+// ----------------------------------------------------------------------------- Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3"
+// (SC'11).  counter (c0..c3), key (k0, k1); 10 rounds with the published
+// multipliers and Weyl increments.
+struct Philox4 { unsigned int v[4]; };
+
+__device__ __forceinline__ Philox4 philox4x32_10(unsigned int c0, unsigned int c1, unsigned int c2,
+                                                 unsigned int c3, unsigned int k0, unsigned int k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned int hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const unsigned int hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const unsigned int n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return Philox4{{c0, c1, c2, c3}};
+}
+
+// uniform in (0, 1] from a 53-bit integer (a << 21) | (b >> 11)
+__device__ __forceinline__ double unit53(unsigned int a, unsigned int b) {
+  const unsigned long long n = ((unsigned long long)a << 21) | (unsigned long long)(b >> 11);
+  return ((double)n + 1.0) * 0x1.0p-53;
+}
+
+// Box-Muller pair from one Philox call
+__device__ __forceinline__ cplx<double> gauss_pair(Philox4 w) {
+  const double u1 = unit53(w.v[0], w.v[1]), u2 = unit53(w.v[2], w.v[3]);
+  const double rho = sqrt(-2.0 * log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  return cplx<double>{rho * cs, rho * sn};
+}
+
+enum { STREAM_MOMENTUM = 1, STREAM_PSEUDOFERMION = 2, STREAM_ACCEPT = 3 };
+
+// pi(x): Re, Im ~ N(0, 1); counter (site, 0, STREAM_MOMENTUM, traj)
+__global__ void draw_momenta(cplx<double>* pi, long V, unsigned long long seed, unsigned int traj) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x)
+    pi[i] = gauss_pair(philox4x32_10((unsigned)i, 0u, STREAM_MOMENTUM, traj, (unsigned)seed, (unsigned)(seed >> 32)));
+}
+
+// R_k(x, s): density exp(-|R|^2); counter (site, 4k + s, STREAM_PSEUDOFERMION, traj)
+__global__ void draw_sources(cplx<double>* R, int npf, long V, unsigned long long seed, unsigned int traj) {
+  const long n = (long)npf * V * 4;
+  const double sc = 0.70710678118654752440;  // sqrt(1/2)
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(i & 3);
+    const long site = (i >> 2) % V;
+    const int k = (int)((i >> 2) / V);
+    const cplx<double> z = gauss_pair(
+        philox4x32_10((unsigned)site, (unsigned)(4 * k + s), STREAM_PSEUDOFERMION, traj, (unsigned)seed,
+                      (unsigned)(seed >> 32)));
+    R[i] = cplx<double>{sc * z.x, sc * z.y};
+  }
+}
+
+// partials of sum Re[conj(a) b] over n complex values, grid (nblk)
+__global__ void dot_re_partials(const cplx<double>* a, const cplx<double>* b, long n, double* part) {
+  __shared__ double red[33];
+  double t = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    t += re_conj_mul(a[i], b[i]);
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = t;
+}
+
+// phi += eps * pi (FP64 and its FP32 copy)
+__global__ void update_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* pi, double eps, long V) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
+    const cplx<double> f = phi[i] + eps * pi[i];
+    phi[i] = f;
+    phi32[i] = cplx<float>{(float)f.x, (float)f.y};
+  }
+}
+
+// pi -= eps * G
+__global__ void update_pi(cplx<double>* pi, const cplx<double>* G, double eps, long V) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x)
+    pi[i] = pi[i] - eps * G[i];
+}
+
+// Metropolis on the device: sums the H partials in a fixed order, draws u and
+// decides.  out = [H0, H1, dH, u, accept]
+struct HParts {
+  const double* kin0; int nkin0;   // sum |pi|^2 at the start
+  const double* sb0; int nsb0;     // S_B at the start
+  const double* spf0; int nspf0;   // sum |R|^2
+  const double* kin1; int nkin1;
+  const double* sb1; int nsb1;
+  const double* spf1; int nspf1;   // sum Re eta^dag X at the end
+};
+
+__device__ __forceinline__ double serial_sum(const double* p, int n) {
+  double t = 0.0;
+  for (int i = 0; i < n; ++i) t += p[i];
+  return t;
+}
+
+__global__ void metropolis(HParts h, double* out, unsigned long long seed, unsigned int traj) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double H0 = 0.5 * serial_sum(h.kin0, h.nkin0) + serial_sum(h.sb0, h.nsb0) + serial_sum(h.spf0, h.nspf0);
+  const double H1 = 0.5 * serial_sum(h.kin1, h.nkin1) + serial_sum(h.sb1, h.nsb1) + serial_sum(h.spf1, h.nspf1);
+  const double dH = H1 - H0;
+  const Philox4 w = philox4x32_10(0u, 0u, STREAM_ACCEPT, traj, (unsigned)seed, (unsigned)(seed >> 32));
+  const double u = unit53(w.v[0], w.v[1]);
+  const bool acc = dH <= 0.0 || u <= exp(-dH);
+  out[0] = H0;
+  out[1] = H1;
+  out[2] = dH;
+  out[3] = u;
+  out[4] = acc ? 1.0 : 0.0;
+}
+
+// on rejection: phi = phi0 (FP64 and FP32 copies)
+__global__ void restore_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* phi0, const double* res, long V) {
+  if (res[4] != 0.0) return;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
+    phi[i] = phi0[i];
+    phi32[i] = cplx<float>{(float)phi0[i].x, (float)phi0[i].y};
+  }
+}
+
+}  // namespace wz

@@ -228,6 +228,7 @@ enum ZTMul {
   ZT_DSLASH = 0,   // out = sign * i h gamma.sin p  in
   ZT_M0INV,        // out = (-Dslash + m^* P_+ + m P_-) / den  in
   ZT_M0INV_DAG,    // out = ( Dslash + m P_+ + m^* P_-) / den  in
+  ZT_SCALAR,       // periodic scalar pair packed in spin slots: slot 0 *= D2(p), slot 1 *= K(p)
 };
 
 template <typename R> struct ZTArgs {
@@ -235,6 +236,8 @@ template <typename R> struct ZTArgs {
   const R* hV;         // h(p) / V
   const R* hdV;        // h(p) / (den(p) V)
   const R* dV;         // 1 / (den(p) V)
+  const R* d2sV;       // D2(p) / V on the periodic grid (ZT_SCALAR)
+  const R* ksV;        // K(p) / V = (1 - D2(p)/2) / V on the periodic grid (ZT_SCALAR)
   const R* sinT;       // sin p_t  (antiperiodic momenta), length T
   const R* sinZ;
   const R* sinY;
@@ -294,7 +297,8 @@ zt_pass(ZTArgs<R> a) {
   // ---------------- z-phase (forward): thread owns (t = q, column, s)
   if (q < NT) {
     const int t = q;
-    const cplx<R> tw{a.twc[t], -a.tws[t]};  // exp(-i pi t / T)
+    // exp(-i pi t / T) for the antiperiodic fermion; 1 for the periodic scalar
+    const cplx<R> tw = MUL == ZT_SCALAR ? cplx<R>{R(1), R(0)} : cplx<R>{a.twc[t], -a.tws[t]};
 #pragma unroll
     for (int z = 0; z < NZ; ++z) v[z] = colok ? tw * A[((long)t * ZXY + (long)z * a.XY) * 4] : cplx<R>{R(0), R(0)};
     fft_ptr<NZ, -1, R>(v);
@@ -334,7 +338,10 @@ zt_pass(ZTArgs<R> a) {
       ww.x = __shfl_sync(0xffffffffu, v[pt].x, ulane + 1);
       ww.y = __shfl_sync(0xffffffffu, v[pt].y, ulane + 1);
       const cplx<R> g = cu * u + cw * ww;  // (gamma . sin p  in)_s
-      if constexpr (MUL == ZT_DSLASH) {
+      if constexpr (MUL == ZT_SCALAR) {
+        const R sc = s == 0 ? a.d2sV[pidx] : (s == 1 ? a.ksV[pidx] : R(0));
+        v[pt] = sc * v[pt];
+      } else if constexpr (MUL == ZT_DSLASH) {
         const R hh = a.sign * a.hV[pidx];
         v[pt] = hh * mul_i(g);
       } else {
@@ -355,7 +362,7 @@ zt_pass(ZTArgs<R> a) {
   // ---------------- z-phase (inverse) and untwist exp(+i pi t / T)
   if (q < NT) {
     const int t = q;
-    const cplx<R> tw{a.twc[t], a.tws[t]};
+    const cplx<R> tw = MUL == ZT_SCALAR ? cplx<R>{R(1), R(0)} : cplx<R>{a.twc[t], a.tws[t]};
 #pragma unroll
     for (int z = 0; z < NZ; ++z) v[z] = sm[((t * NZ + z) * C + c) * 4 + s];
     fft_ptr<NZ, +1, R>(v);

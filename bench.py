@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory timing")
+    ap.add_argument("--hmc-traj", type=int, default=2, help="timed trajectories per precision")
     return ap.parse_args()
 
 
@@ -269,6 +271,33 @@ def main():
                 "iterations": st64["iterations"], "max_true_residual": st64["max_true_residual"],
                 "mixed_speedup_per_solve": ms64 / (total_ms / args.steps)}
 
+    # HMC trajectories/s on the differentiation workload (16^4, m = 0.1, g = 0.5,
+    # one pseudofermion, tau = 1, 20 leapfrog steps), mixed and FP64 solves
+    hmc = None
+    if not args.no_hmc:
+        hw = synth.FORCE_16
+        hlat = wz.Lattice(hw.dims, m=hw.m, g=hw.g, stream=stream.cuda_stream)
+        hmc = {"workload": f"{hw.name}: 16^4, m={hw.m}, g={hw.g}, phi sigma {hw.sigma}, 1 pseudofermion, "
+                           f"tau={hw.extra['tau']}, {hw.extra['nsteps']} leapfrog steps, CG to 1e-10"}
+        for label, flags in (("mixed", 0), ("fp64", wz.WZ_HMC_FP64_SOLVES)):
+            hlat.set_phi(torch.from_numpy(synth.scalar_field(hw.dims, hw.sigma, 0)).cuda())
+            kw = dict(tau=hw.extra["tau"], nsteps=hw.extra["nsteps"], npf=1, tol=1e-10, seed=2024, flags=flags)
+            hlat.trajectory(traj_index=0, **kw)  # warm-up
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sts = []
+            e0.record(stream)
+            for t in range(args.hmc_traj):
+                sts.append(hlat.trajectory(traj_index=1 + t, **kw))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            hmc[label] = {"traj_per_s": args.hmc_traj / (ms / 1000.0), "ms_per_traj": ms / args.hmc_traj,
+                          "cg_iterations_per_traj": float(np.mean([x["cg_iterations"] for x in sts])),
+                          "dH": [round(x["dH"], 5) for x in sts], "accept": [x["accept"] for x in sts]}
+        hmc["mixed_speedup"] = hmc["fp64"]["ms_per_traj"] / hmc["mixed"]["ms_per_traj"]
+        hlat.close()
+
     # end to end through the C ABI with pinned host buffers
     hb = torch.from_numpy(b).pin_memory()
     hx = torch.zeros_like(hb).pin_memory()
@@ -314,7 +343,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
         }))
     lat.close()

@@ -103,6 +103,13 @@ __device__ __forceinline__ double sum_partials(const double* part, int nblk) {
 
 template <typename R> __device__ __forceinline__ R norm2(cplx<R> a) { return a.x * a.x + a.y * a.y; }
 
+// TMA bulk prefetch of a contiguous global range into L2 (16-byte aligned,
+// size a multiple of 16): the phase-B operands of a plane are requested at
+// block entry and arrive while the block is busy with its phase-A FFT.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename R, typename LO, int L, int MODE, bool PC>
 __global__ void __launch_bounds__(XYShape<L>::THREADS)
 xy_cg(CGArgs<R, LO> a) {
@@ -132,6 +139,31 @@ xy_cg(CGArgs<R, LO> a) {
   cplx<R> v[L];
   R part = R(0);
 
+  // operands of phase B, distinct arrays (lets the compiler hoist loads above stores)
+  cplx<R>* __restrict__ Pp = a.p;
+  cplx<R>* __restrict__ Pr = a.r;
+  cplx<R>* __restrict__ Px = a.x;
+  cplx<R>* __restrict__ Pc = a.Cb;
+  const cplx<R>* __restrict__ Pb = a.b;
+  cplx<LO>* __restrict__ Plx = a.lo_x;
+  cplx<LO>* __restrict__ Plr = a.lo_r;
+  if (live && (tid % S::TPP) == 0) {
+    constexpr unsigned PB = L * L * 4 * sizeof(cplx<R>);
+    const long pe = plane * (long)(L * L) * 4;
+    if constexpr (MODE == CG_P5) {
+      prefetch_l2(Pp + pe, PB);
+      prefetch_l2(Pc + pe, PB);
+      prefetch_l2(Px + pe, PB);
+      prefetch_l2(Pr + pe, PB);
+    } else if constexpr (MODE == CG_P3) {
+      prefetch_l2(Pp + pe, PB);
+    } else if constexpr (MODE == RU_P5) {
+      prefetch_l2(Pp + pe, PB);
+      prefetch_l2(Pc + pe, PB);
+      prefetch_l2(Pb + pe, PB);
+    }
+  }
+
   if constexpr (MODE == CG_P5) {
     // alpha = rr / p.Ap from the P3 partials: the same sum in every block
     if (tid < 32) {
@@ -158,38 +190,38 @@ xy_cg(CGArgs<R, LO> a) {
       const long e = (site0 + y * L) * 4 + s;
       if constexpr (MODE == CG_P1) {
         // beta == 0 (first step): p = r without reading the previous p
-        const cplx<R> pv = beta != R(0) ? a.r[e] + beta * a.p[e] : a.r[e];
-        a.p[e] = pv;
+        const cplx<R> pv = beta != R(0) ? Pr[e] + beta * Pp[e] : Pr[e];
+        Pp[e] = pv;
         v[y] = pv;
       } else if constexpr (MODE == CG_P3) {
-        const cplx<R> pe = a.p[e];
+        const cplx<R> pe = Pp[e];
         const cplx<R> f = a.phi[phib + y * L];
         if constexpr (PC) v[y] = pe + site_coef<R, false, false>(a.k, f, s) * v[y];
         else v[y] = v[y] + site_coef<R, false, true>(a.k, f, s) * pe;
-        a.Cb[e] = v[y];
+        Pc[e] = v[y];
         part += norm2(v[y]) + sigma * norm2(pe);
         if constexpr (PC) v[y] = site_coef<R, true, false>(a.k, f, s) * v[y];
       } else if constexpr (MODE == CG_P5 || MODE == RU_P5) {
-        const cplx<R> pe = a.p[e];  // p, or x_hi for RU_P5
+        const cplx<R> pe = Pp[e];  // p, or x_hi for RU_P5
         cplx<R> ap;
-        if constexpr (PC) ap = a.Cb[e] + v[y];
-        else ap = v[y] + site_coef<R, true, true>(a.k, a.phi[phib + y * L], s) * a.Cb[e];
+        if constexpr (PC) ap = Pc[e] + v[y];
+        else ap = v[y] + site_coef<R, true, true>(a.k, a.phi[phib + y * L], s) * Pc[e];
         ap = ap + sigma * pe;
         if constexpr (MODE == CG_P5) {
-          a.x[e] = a.x[e] + alpha * pe;
-          const cplx<R> rn = a.r[e] - alpha * ap;
-          a.r[e] = rn;
+          Px[e] = Px[e] + alpha * pe;
+          const cplx<R> rn = Pr[e] - alpha * ap;
+          Pr[e] = rn;
           part += norm2(rn);
         } else {
-          const cplx<R> rn = a.b[e] - ap;
-          a.lo_r[e] = cplx<LO>{(LO)rn.x, (LO)rn.y};
+          const cplx<R> rn = Pb[e] - ap;
+          Plr[e] = cplx<LO>{(LO)rn.x, (LO)rn.y};
           part += norm2(rn);
         }
       } else if constexpr (MODE == RU_P1) {
-        const cplx<LO> xl = a.lo_x[e];
-        const cplx<R> xv = a.p[e] + cplx<R>{(R)xl.x, (R)xl.y};
-        a.p[e] = xv;
-        a.lo_x[e] = cplx<LO>{LO(0), LO(0)};
+        const cplx<LO> xl = Plx[e];
+        const cplx<R> xv = Pp[e] + cplx<R>{(R)xl.x, (R)xl.y};
+        Pp[e] = xv;
+        Plx[e] = cplx<LO>{LO(0), LO(0)};
         v[y] = xv;
       }
     }

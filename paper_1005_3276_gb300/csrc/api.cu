@@ -56,7 +56,8 @@ bool zt_supported(int nz, int nt) {
 // One thread per fermion momentum p = (pi(2nt+1)/T, 2pi nz/Z, 2pi ny/Y, 2pi nx/X):
 //   b = M0 - r sum_mu 2 sin^2(p_mu/2),  omega = sqrt(b^2 + sum sin^2 p_mu),
 //   h = 2/(omega + b),  den = h^2 sum sin^2 p_mu + |m|^2              (Sec. 3.1, 7.3)
-// Evaluated in FP64; the FP32 table is the rounded FP64 value.
+// Evaluated in FP64; the FP32 table is the rounded FP64 value.  Tables are
+// stored in the xy-transposed momentum order [pt][pz][px][py] of the zt pass.
 struct TableArgs {
   int T, Z, Y, X;
   double r, M0, m2, invV;
@@ -84,12 +85,14 @@ __global__ void momentum_tables_kernel(TableArgs a) {
     const double omega = sqrt(b * b + s2);
     const double h = 2.0 / (omega + b);
     const double den = h * h * s2 + a.m2;
-    a.hV[i] = h * a.invV;
-    a.hdV[i] = h / den * a.invV;
-    a.dV[i] = a.invV / den;
-    a.hVf[i] = (float)a.hV[i];
-    a.hdVf[i] = (float)a.hdV[i];
-    a.dVf[i] = (float)a.dV[i];
+    // stored in the xy-transposed momentum order of the zt pass: [pt][pz][px][py]
+    const long j = (((long)nt * a.Z + nz) * a.X + nx) * a.Y + ny;
+    a.hV[j] = h * a.invV;
+    a.hdV[j] = h / den * a.invV;
+    a.dV[j] = a.invV / den;
+    a.hVf[j] = (float)a.hV[j];
+    a.hdVf[j] = (float)a.hdV[j];
+    a.dVf[j] = (float)a.dV[j];
     // scalar symbols on the periodic grid (p_t = 2 pi nt / T): D2 = 1 - b/omega,
     // K = 1 - D2/2 (Eq. acws); at the zone corners sum sin^2 = 0 and omega = |b|
     double s2p = 0.0, wp = 0.0;
@@ -102,10 +105,10 @@ __global__ void momentum_tables_kernel(TableArgs a) {
     const double bp = a.M0 - a.r * wp;
     const double op = sqrt(bp * bp + s2p);
     const double D2 = op > 0.0 ? 1.0 - bp / op : 1.0;
-    a.d2sV[i] = D2 * a.invV;
-    a.ksV[i] = (1.0 - 0.5 * D2) * a.invV;
-    a.d2sVf[i] = (float)a.d2sV[i];
-    a.ksVf[i] = (float)a.ksV[i];
+    a.d2sV[j] = D2 * a.invV;
+    a.ksV[j] = (1.0 - 0.5 * D2) * a.invV;
+    a.d2sVf[j] = (float)a.d2sV[j];
+    a.ksVf[j] = (float)a.ksV[j];
   }
 }
 

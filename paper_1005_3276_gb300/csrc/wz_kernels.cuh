@@ -102,10 +102,12 @@ template <int L> struct XYShape {
 // the plane P in shared memory (row pitch RP, one site of padding per row).
 template <typename R, int L> struct XYPhase {
   using S = XYShape<L>;
-  // phase A: inverse FFT along x of momentum row y = w (global), result into P
+  // phase A: inverse FFT along x of momentum row p_y = w (global), result into P.
+  // Momentum-space planes are stored xy-transposed, [p_x][p_y][spin], so that
+  // the lanes of a warp (consecutive p_y, spin) read one contiguous run.
   static __device__ __forceinline__ void inv_x(const cplx<R>* Ap, cplx<R>* P, int w, int s, cplx<R> (&v)[L]) {
 #pragma unroll
-    for (int x = 0; x < L; ++x) v[x] = Ap[(w * L + x) * 4 + s];
+    for (int x = 0; x < L; ++x) v[x] = Ap[(x * L + w) * 4 + s];
     fft_line<L, +1, R>(v);
 #pragma unroll
     for (int x = 0; x < L; ++x) P[w * S::RP + x * 4 + s] = v[x];
@@ -124,12 +126,13 @@ template <typename R, int L> struct XYPhase {
     for (int y = 0; y < L; ++y) P[y * S::RP + w * 4 + s] = v[y];
   }
   // phase C: row p_y = w of P, forward FFT along x, store momentum output
+  // (xy-transposed, see inv_x)
   static __device__ __forceinline__ void fwd_x(const cplx<R>* P, cplx<R>* Ap, int w, int s, cplx<R> (&v)[L]) {
 #pragma unroll
     for (int x = 0; x < L; ++x) v[x] = P[w * S::RP + x * 4 + s];
     fft_line<L, -1, R>(v);
 #pragma unroll
-    for (int x = 0; x < L; ++x) Ap[(w * L + x) * 4 + s] = v[x];
+    for (int x = 0; x < L; ++x) Ap[(x * L + w) * 4 + s] = v[x];
   }
 };
 
@@ -155,13 +158,7 @@ xy_pass(XYArgs<R> a) {
 
   // ---------------- phase A: inverse FFT along x of the momentum input
   if (I::inv) {
-    if (live) {
-#pragma unroll
-      for (int x = 0; x < L; ++x) v[x] = a.A_in[base + (w * L + x) * 4 + s];
-      fft_line<L, +1, R>(v);
-#pragma unroll
-      for (int x = 0; x < L; ++x) P[w * S::RP + x * 4 + s] = v[x];
-    }
+    if (live) XYPhase<R, L>::inv_x(a.A_in + base, P, w, s, v);
     __syncthreads();
   }
 
@@ -214,13 +211,7 @@ xy_pass(XYArgs<R> a) {
   __syncthreads();
 
   // ---------------- phase C: forward FFT along x, store momentum output
-  if (live) {
-#pragma unroll
-    for (int x = 0; x < L; ++x) v[x] = P[w * S::RP + x * 4 + s];
-    fft_line<L, -1, R>(v);
-#pragma unroll
-    for (int x = 0; x < L; ++x) a.A_out[base + (w * L + x) * 4 + s] = v[x];
-  }
+  if (live) XYPhase<R, L>::fwd_x(P, a.A_out + base, w, s, v);
 }
 
 // ----------------------------------------------------------------------------- zt pass
@@ -257,7 +248,9 @@ template <typename R> struct ZTArgs {
 // Columns per block: 256 B contiguous per (z, t) row for short lines, fewer
 // columns for long lines so that a block stays at <= 512 threads.
 template <typename R, int NMAX> struct ZTTile {
-  static constexpr int C0 = sizeof(R) == 4 ? 8 : 4;
+  // 4 columns = 128 B (FP32) / 256 B (FP64) contiguous per (z, t) row; at
+  // 16^2 this gives 256-thread blocks, two of which fit an SM
+  static constexpr int C0 = 4;
   static constexpr int C = NMAX <= 16 ? C0 : (NMAX <= 32 ? C0 / 2 : C0 / 4);
 };
 
@@ -283,7 +276,7 @@ zt_pass(ZTArgs<R> a) {
   const int rhs = blockIdx.x / a.ntiles;
   if (a.gate && !a.gate[(long)rhs * a.gate_stride]) return;  // whole block, before any barrier
   if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
-  const int col_raw = (blockIdx.x % a.ntiles) * C + c;  // (y, x) column = y * X + x
+  const int col_raw = (blockIdx.x % a.ntiles) * C + c;  // (p_x, p_y) column = p_x * Y + p_y
   // the last tile may be ragged (X * Y not a multiple of C): lanes past the
   // end keep computing on zeros so that every warp stays whole for the
   // shuffles, but never touch memory
@@ -314,7 +307,8 @@ zt_pass(ZTArgs<R> a) {
     for (int t = 0; t < NT; ++t) v[t] = sm[((t * NZ + pz) * C + c) * 4 + s];
     fft_ptr<NT, -1, R>(v);
 
-    const int py = col / a.X, px = col - py * a.X;
+    // momentum planes are xy-transposed: column = p_x * Y + p_y (X == Y)
+    const int px = col / a.X, py = col - px * a.X;
     const R sx = a.sinX[px], sy = a.sinY[py], sz = a.sinZ[pz];
     const int lane = threadIdx.x & 31;
     const int ulane = (lane & ~3) | (s < 2 ? 2 : 0);  // opposite-chirality pair

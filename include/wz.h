@@ -31,6 +31,11 @@
  * returns after the results are back in host memory.  The context owns its
  * tables, workspace and RNG state; it is not thread-safe.
  *
+ * Launching: a solve replays a CUDA graph of its iteration loop (a WHILE
+ * conditional node driven by the device-side convergence state), cached on
+ * the context per solve shape; setting WZ_NO_GRAPHS=1 in the environment
+ * before wz_create makes the context launch the same kernels eagerly.
+ *
  * Errors: every call returns a WZ_* status; nothing throws across the ABI.
  * wz_last_error returns a message for the most recent failure of that context.
  */

@@ -1,6 +1,7 @@
 // C ABI entry points: context, tables, phi, apply.
 #include <chrono>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -252,6 +253,10 @@ int wz_create(const wz_params* p, void* stream, wz_ctx** out) {
   c->V = (long)T * Z * Y * X;
   c->stream = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
+  // WZ_NO_GRAPHS=1 in the environment makes the solver launch its chunks
+  // eagerly instead of through the cached CUDA graph (same kernels, same results)
+  const char* ng = getenv("WZ_NO_GRAPHS");
+  c->use_graphs = !(ng && ng[0] == '1');
   int rc = build_tables(c);
   if (rc == WZ_OK) {
     cudaError_t e = cudaMalloc(&c->phi64, sizeof(cplx<double>) * c->V);
@@ -259,6 +264,7 @@ int wz_create(const wz_params* p, void* stream, wz_ctx** out) {
     if (e == cudaSuccess) e = cudaMemsetAsync(c->phi64, 0, sizeof(cplx<double>) * c->V, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->phi32, 0, sizeof(cplx<float>) * c->V, c->stream);
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, WZ_PINNED_BYTES);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) rc = cuda_error(c, e, "wz_create");
   }
@@ -279,6 +285,8 @@ int wz_destroy(wz_ctx* c) {
   if (c->phi64) cudaFree(c->phi64);
   if (c->phi32) cudaFree(c->phi32);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
+  for (auto& g : c->solver_graph) g.release();
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   c->ws_apply.release();
   c->ws_stage.release();
   c->ws_solver.release();

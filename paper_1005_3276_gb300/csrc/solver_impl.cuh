@@ -86,7 +86,7 @@ static int xy_nblk(int L, int TZ) {
 // Workspace layout (bytes) for a solve with iteration type RI.
 template <typename RI> struct SolverWS {
   size_t field_ri, field64, off_xlo, off_r, off_p, off_A, off_C, off_A64, off_C64, off_bt, off_xt, off_part,
-      off_st, total;
+      off_st, off_trips, total;
   SolverWS(long V, int nrhs, int nblk, bool pc) {
     field_ri = sizeof(cplx<RI>) * 4 * (size_t)V * nrhs;
     field64 = sizeof(cplx<double>) * 4 * (size_t)V * nrhs;
@@ -103,10 +103,11 @@ template <typename RI> struct SolverWS {
     off_C = take(field_ri);
     off_A64 = take(field64);
     off_C64 = take(field64);
-    off_bt = pc ? take(field64) : 0;
-    off_xt = pc ? take(field64) : 0;
+    off_bt = take(field64);  // right-hand side of the recursion (b, or b~ when preconditioned)
+    off_xt = take(field64);  // FP64 solution of the recursion (x, or x~)
     off_part = take(sizeof(double) * 3 * (size_t)nrhs * (nblk > 64 ? nblk : 64));
     off_st = take(sizeof(RhsState) * nrhs);
+    off_trips = take(sizeof(int));
     total = o;
   }
 };
@@ -137,15 +138,13 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   const long n_per_rhs = 4L * c->V;
 
   // preconditioned problem: b~ = (M0^-1)^dag b, solve for x~ = M0 x
-  const cplx<double>* bs = b;
-  cplx<double>* xs = x;
+  cplx<double>* bs = (cplx<double>*)(base + W.off_bt);
+  cplx<double>* xs = (cplx<double>*)(base + W.off_xt);
   if (pc) {
-    cplx<double>* bt = (cplx<double>*)(base + W.off_bt);
-    cplx<double>* xt = (cplx<double>*)(base + W.off_xt);
-    int rc = apply_op<double>(c, WZ_OP_M0INV_DAG, b, bt, nrhs, 0.0, A64);
+    int rc = apply_op<double>(c, WZ_OP_M0INV_DAG, b, bs, nrhs, 0.0, A64);
     if (rc) return rc;
-    bs = bt;
-    xs = xt;
+  } else {
+    WZ_CUDA_TRY(c, cudaMemcpyAsync(bs, b, W.field64, cudaMemcpyDeviceToDevice, s));
   }
 
   WZ_CUDA_TRY(c, cudaMemsetAsync(xs, 0, W.field64, s));
@@ -201,7 +200,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   const double delta2 = delta * delta;
   const int K = 8;
   RhsState* hst = (RhsState*)c->host_pinned;
-  if (sizeof(RhsState) * nrhs > WZ_PINNED_SCRATCH_OFFSET) return set_error(c, WZ_EINVAL, "too many right-hand sides");
+  if (sizeof(RhsState) * nrhs > WZ_PINNED_SCRATCH_OFFSET - 64) return set_error(c, WZ_EINVAL, "too many right-hand sides");
   cudaError_t e;
 #define WZ_RUN(...)                                                 \
   do {                                                              \
@@ -209,59 +208,136 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     if (e != cudaSuccess) return cuda_error(c, e, #__VA_ARGS__);    \
   } while (0)
   const int max_chunks = maxiter / K + 64;
+
+  // one chunk: K iterations and one reliable-update block, all gated on the device
+  auto issue_chunk = [&](cudaStream_t q) -> cudaError_t {
+    cudaError_t e2;
+#define WZ_Q(...)                          \
+  do {                                     \
+    e2 = (__VA_ARGS__);                    \
+    if (e2 != cudaSuccess) return e2;      \
+  } while (0)
+    for (int k = 0; k < K; ++k) {
+      CGArgs<RI, RI> a1 = ga;
+      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P1, a1, nrhs, q));
+      WZ_Q(launch_zt<RI>(c->Z, c->T, mul1, z1, nrhs, q));
+      CGArgs<RI, RI> a3 = ga;
+      a3.part_out = part3;
+      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P3, a3, nrhs, q));
+      WZ_Q(launch_zt<RI>(c->Z, c->T, mul2, z2, nrhs, q));
+      CGArgs<RI, RI> a5 = ga;
+      a5.part_in = part3;
+      a5.part_out = part5;
+      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, q));
+      ++g_launches;
+      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, nblk, delta2, maxiter);
+      WZ_Q(cudaGetLastError());
+    }
+    WZ_Q(launch_cg<double, RI>(L, pc, RU_P1, ra, nrhs, q));
+    WZ_Q(launch_zt<double>(c->Z, c->T, mul1, y1, nrhs, q));
+    CGArgs<double, double> r3{};
+    r3.A = A64;
+    r3.Cb = C64;
+    r3.p = xs;
+    r3.phi = c->phi64;
+    r3.k = ra.k;
+    r3.shift = shift;
+    r3.st = st;
+    r3.nblk = nblk;
+    r3.TZ = TZ;
+    r3.gate_ru = 1;
+    WZ_Q(launch_cg<double, double>(L, pc, CG_P3, r3, nrhs, q));
+    WZ_Q(launch_zt<double>(c->Z, c->T, mul2, y2, nrhs, q));
+    CGArgs<double, RI> r5 = ra;
+    r5.part_out = partR;
+    WZ_Q(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, q));
+    ++g_launches;
+    cg_scalar_ru<<<nrhs, 32, 0, q>>>(st, partR, nblk, maxiter);
+    WZ_Q(cudaGetLastError());
+#undef WZ_Q
+    return cudaSuccess;
+  };
+
+  // Graph mode: the whole chunk loop is one CUDA graph whose body sits in a
+  // WHILE conditional node; a one-thread kernel at the end of the body keeps
+  // the loop going while some RHS is active, and stops it after max_chunks
+  // trips in any case.  The graph only references workspace buffers, so it is
+  // cached on the context and replayed by every solve of the same shape.
+  // The kernel probe needs eager launches (it brackets each launch).
+  const bool use_graph = c->use_graphs && !g_probe.active;
+  SolverGraph& G = c->solver_graph[sizeof(RI) == 4 ? 0 : 1];
+  int* trips = (int*)(base + W.off_trips);
+  if (use_graph) {
+    SolverGraphKey key{};
+    key.nrhs = nrhs;
+    key.pc = pc;
+    key.shift = shift;
+    key.maxiter = maxiter;
+    key.delta2 = delta2;
+    key.ws = c->ws_solver.ptr;
+    key.ws_bytes = c->ws_solver.bytes;
+    key.phi64 = c->phi64;
+    key.phi32 = c->phi32;
+    if (!G.exec || memcmp(&key, &G.key, sizeof(key)) != 0) {
+      G.release();
+      WZ_CUDA_TRY(c, cudaGraphCreate(&G.graph, 0));
+      cudaGraphConditionalHandle h;
+      WZ_CUDA_TRY(c, cudaGraphConditionalHandleCreate(&h, G.graph, 1, cudaGraphCondAssignDefault));
+      cudaGraphNodeParams np{};
+      np.type = cudaGraphNodeTypeConditional;
+      np.conditional.handle = h;
+      np.conditional.type = cudaGraphCondTypeWhile;
+      np.conditional.size = 1;
+      cudaGraphNode_t node;
+      WZ_CUDA_TRY(c, cudaGraphAddNode(&node, G.graph, nullptr, nullptr, 0, &np));
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      WZ_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
+                                                   cudaStreamCaptureModeRelaxed));
+      const unsigned long long l0 = g_launches;
+      cudaError_t ce = issue_chunk(c->cap_stream);
+      if (ce == cudaSuccess) {
+        ++g_launches;
+        cg_loop_cond<<<1, 32, 0, c->cap_stream>>>(h, st, nrhs, trips, max_chunks);
+        ce = cudaGetLastError();
+      }
+      G.body_launches = g_launches - l0;  // kernels per trip of the WHILE body
+      g_launches = l0;                    // capturing launches nothing
+      cudaGraph_t captured = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &captured);
+      if (ce != cudaSuccess) return cuda_error(c, ce, "solver graph capture");
+      if (ee != cudaSuccess) return cuda_error(c, ee, "cudaStreamEndCapture");
+      WZ_CUDA_TRY(c, cudaGraphInstantiate(&G.exec, G.graph, 0));
+      G.key = key;
+    }
+  }
+
   // The preconditioned recursion stops on the residual of M~^dag M~ x~ = b~;
   // the original residual b - M^dag M x = M0^dag (b~ - M~^dag M~ x~) is then
   // checked in FP64 and RHS that miss tol resume with a tighter tolerance.
   std::vector<double> rel(nrhs);
   for (int outer = 0; outer < 8; ++outer) {
-  for (int chunk = 0; chunk < max_chunks; ++chunk) {
-    for (int k = 0; k < K; ++k) {
-      CGArgs<RI, RI> a1 = ga;
-      WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P1, a1, nrhs, s));
-      WZ_RUN(launch_zt<RI>(c->Z, c->T, mul1, z1, nrhs, s));
-      CGArgs<RI, RI> a3 = ga;
-      a3.part_out = part3;
-      WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P3, a3, nrhs, s));
-      WZ_RUN(launch_zt<RI>(c->Z, c->T, mul2, z2, nrhs, s));
-      CGArgs<RI, RI> a5 = ga;
-      a5.part_in = part3;
-      a5.part_out = part5;
-      WZ_RUN(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, s));
-      ++g_launches;
-      cg_scalar_iter<<<nrhs, 32, 0, s>>>(st, part5, nblk, delta2, maxiter);
-      WZ_RUN(cudaGetLastError());
-    }
-    // reliable update / true residual for the RHS that asked for one
-    WZ_RUN(launch_cg<double, RI>(L, pc, RU_P1, ra, nrhs, s));
-    WZ_RUN(launch_zt<double>(c->Z, c->T, mul1, y1, nrhs, s));
-    {
-      CGArgs<double, double> r3{};
-      r3.A = A64;
-      r3.Cb = C64;
-      r3.p = xs;
-      r3.phi = c->phi64;
-      r3.k = ra.k;
-      r3.shift = shift;
-      r3.st = st;
-      r3.nblk = nblk;
-      r3.TZ = TZ;
-      r3.gate_ru = 1;
-      WZ_RUN(launch_cg<double, double>(L, pc, CG_P3, r3, nrhs, s));
-    }
-    WZ_RUN(launch_zt<double>(c->Z, c->T, mul2, y2, nrhs, s));
-    CGArgs<double, RI> r5 = ra;
-    r5.part_out = partR;
-    WZ_RUN(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, s));
-    ++g_launches;
-    cg_scalar_ru<<<nrhs, 32, 0, s>>>(st, partR, nblk, maxiter);
-    WZ_RUN(cudaGetLastError());
+  if (use_graph) {
+    WZ_RUN(cudaMemsetAsync(trips, 0, sizeof(int), s));
+    WZ_RUN(cudaGraphLaunch(G.exec, s));
     WZ_RUN(cudaMemcpyAsync(hst, st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, s));
+    int* htrips = (int*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET - 64);
+    WZ_RUN(cudaMemcpyAsync(htrips, trips, sizeof(int), cudaMemcpyDeviceToHost, s));
     WZ_RUN(cudaStreamSynchronize(s));
-    bool any = false;
-    for (int j = 0; j < nrhs; ++j) any |= hst[j].active != 0;
-    if (!any) break;
+    g_launches += (unsigned long long)(*htrips) * G.body_launches;
+  } else {
+    for (int chunk = 0; chunk < max_chunks; ++chunk) {
+      WZ_RUN(issue_chunk(s));
+      WZ_RUN(cudaMemcpyAsync(hst, st, sizeof(RhsState) * nrhs, cudaMemcpyDeviceToHost, s));
+      WZ_RUN(cudaStreamSynchronize(s));
+      bool any = false;
+      for (int j = 0; j < nrhs; ++j) any |= hst[j].active != 0;
+      if (!any) break;
+    }
   }
-  if (!pc) break;
+  if (!pc) {
+    WZ_RUN(cudaMemcpyAsync(x, xs, W.field64, cudaMemcpyDeviceToDevice, s));
+    break;
+  }
   {
     int rc = apply_op<double>(c, WZ_OP_M0INV, xs, x, nrhs, 0.0, A64);
     if (rc) return rc;

@@ -318,4 +318,14 @@ static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, 
   }
 }
 
+// Condition of the solver graph's WHILE node: continue while some RHS is
+// active, and never beyond cap trips.
+static __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const RhsState* st, int nrhs, int* trips, int cap) {
+  if (threadIdx.x != 0) return;
+  int any = 0;
+  for (int j = 0; j < nrhs; ++j) any |= st[j].active;
+  const int t = ++*trips;
+  cudaGraphSetConditional(h, (any && t < cap) ? 1u : 0u);
+}
+
 }  // namespace wz

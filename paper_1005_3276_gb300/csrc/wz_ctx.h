@@ -49,6 +49,32 @@ struct DevBuf {
   }
 };
 
+// Cached CUDA graph of the solver's chunk loop and what it was captured for.
+struct SolverGraphKey {
+  int nrhs;
+  int pc;
+  double shift;
+  int maxiter;
+  double delta2;
+  void* ws;
+  size_t ws_bytes;
+  const void* phi64;
+  const void* phi32;
+};
+struct SolverGraph {
+  SolverGraphKey key{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long body_launches = 0;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    key = SolverGraphKey{};
+  }
+};
+
 }  // namespace wz
 
 struct wz_ctx {
@@ -73,6 +99,10 @@ struct wz_ctx {
   // small pinned block for scalar read-back: [0, WZ_PINNED_SCRATCH_OFFSET) holds
   // the solver's per-RHS state, the rest is scratch for other reductions
   void* host_pinned = nullptr;
+  // solver graphs (index 0: mixed FP32 iteration, 1: FP64) and their capture stream
+  bool use_graphs = true;
+  cudaStream_t cap_stream = nullptr;
+  wz::SolverGraph solver_graph[2];
 };
 
 #define WZ_PINNED_BYTES (256 * 1024)

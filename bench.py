@@ -227,7 +227,6 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     launches0 = wz.wz_kernel_launches()
-    wz.wz_probe_begin(args.probe, args.probe_bytes)
     total_ms, total_applies, stats = 0.0, 0, []
     for _ in range(args.steps):
         flush.zero_()
@@ -242,9 +241,19 @@ def main():
         total_ms += e0.elapsed_time(e1)
         total_applies += n
         stats.append(st)
-    probe = wz.wz_probe_end()
     launches = wz.wz_kernel_launches() - launches0
     clk = clocks.stop()
+
+    # Roofline of the dominant kernel: one more step of the same workload with
+    # the library's probe armed (CUDA events around every launch of the
+    # kernel class on the launching stream; the probe makes the solver launch
+    # its kernels one by one instead of replaying its graph, the kernels are
+    # the same).
+    flush.zero_()
+    torch.cuda.synchronize()
+    wz.wz_probe_begin(args.probe, args.probe_bytes)
+    solve()
+    probe = wz.wz_probe_end()
 
     # max time over ranks, sum of work over ranks
     t_max, applies_all = total_ms, total_applies

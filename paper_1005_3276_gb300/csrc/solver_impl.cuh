@@ -31,10 +31,10 @@ static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st
   double site = 0.0;
   int kind = PK_CG_P1;
   switch (MODE) {
-    case CG_P1: site = 4 * f; kind = PK_CG_P1; break;                 // r, p in; p, A out
+    case CG_P1: site = 6 * f; kind = PK_CG_P1; break;                 // r, p, x in; p, A, x out
     case CG_P3: site = 4 * f + ph; kind = PK_CG_P3; break;            // A, p in; C, A out; phi
-    case CG_P5: site = 7 * f + (PC ? 0 : ph); kind = PK_CG_P5; break; // A, p, C, x, r in; x, r out
-    case RU_P1: site = 3 * f + 2 * lo; kind = PK_RU_P1; break;        // x_hi, x_lo in; x_hi, x_lo, A out
+    case CG_P5: site = (a.shift != 0.0 ? 5 : 4) * f + (PC ? 0 : ph); kind = PK_CG_P5; break;  // A, C, r (p) in; r out
+    case RU_P1: site = 3 * f + 3 * lo; kind = PK_RU_P1; break;        // x_hi, x_lo, p in; x_hi, x_lo, A out
     case RU_P5: site = 4 * f + lo + (PC ? 0 : ph); kind = PK_RU_P5; break;  // A, x_hi, C, b in; r out
   }
   const double blk_bytes = site * L * L * S::PPC;
@@ -177,6 +177,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   ra.Cb = C64;
   ra.p = xs;  // x_hi
   ra.lo_x = xlo;
+  ra.lo_p = p;
   ra.lo_r = r;
   ra.b = bs;
   ra.phi = c->phi64;
@@ -230,7 +231,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       a5.part_out = part5;
       WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, q));
       ++g_launches;
-      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, nblk, delta2, maxiter);
+      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter);
       WZ_Q(cudaGetLastError());
     }
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P1, ra, nrhs, q));

@@ -5,16 +5,17 @@
 // recursion per right-hand side, all right-hand sides in the same launches.
 // One iteration is five plane passes plus a one-warp-per-RHS scalar kernel:
 //
-//   P1 (xy)  p = r + beta p ; A = F_xy p
+//   P1 (xy)  x += alpha' p (alpha' of the previous iteration) ; p = r + beta p ; A = F_xy p
 //   P2 (zt)  A <- Dslash(p) A                  (M0^-1(p) when preconditioned)
 //   P3 (xy)  C = M p (position space) ; A = F_xy C' ; partial |C|^2 + sigma |p|^2
 //   P4 (zt)  A <- -Dslash(p) A                 ((M0^-1)^dag(p) when preconditioned)
-//   P5 (xy)  Ap = M^dag C + sigma p ; alpha = rr / (p.Ap) ; x += alpha p ;
-//            r -= alpha Ap ; partial |r|^2
+//   P5 (xy)  Ap = M^dag C + sigma p ; alpha = rr / (p.Ap) ; r -= alpha Ap ;
+//            partial |r|^2
 //   S        rr_new, beta = rr_new / rr, reliable-update and stop tests
 //
-// p.Ap = |M p|^2 + sigma |p|^2 is known after P3, so P5 does the vector
-// updates without storing Ap.  Reductions are deterministic: per-thread
+// p.Ap = |M p|^2 + sigma |p|^2 is known after P3, so P5 updates r without
+// storing Ap; the x update of an iteration is deferred to the next P1, which
+// reads p anyway (or to the reliable update, which folds it in).  Reductions are deterministic: per-thread
 // partials, a fixed warp/block tree, one partial per block, and every
 // consumer sums the block partials in the same order.
 //
@@ -23,7 +24,7 @@
 // times its value at the last update (or below tol |b|), the FP32 iterate is
 // folded into the FP64 solution and the residual is recomputed in FP64:
 //
-//   RU_P1 (xy, FP64) x_hi += x_lo ; x_lo = 0 ; A = F_xy x_hi
+//   RU_P1 (xy, FP64) x_hi += x_lo + alpha p (the pending update) ; x_lo = 0 ; A = F_xy x_hi
 //   zt, P3, zt       (FP64 M^dagger M as above)
 //   RU_P5 (xy, FP64) r = b - (M^dag M + sigma) x_hi ; r_lo = (float) r ; partial |r|^2
 //   S_ru             converged if |r| <= tol |b|, else beta = |r|^2 / rr_prev
@@ -43,6 +44,7 @@ struct RhsState {
   double rmax2;    // |r|^2 at the last reliable update
   double rtrue2;   // |b - A x|^2 at the last reliable update (FP64)
   double tol2;     // stop when |b - A x|^2 <= tol2 |b|^2
+  double alpha;    // alpha of the last iteration, whose x += alpha p is still pending
   int run;         // iteration passes act on this RHS
   int ru;          // reliable update pending
   int active;      // not finished
@@ -60,6 +62,7 @@ template <typename R, typename LO> struct CGArgs {
   cplx<R>* r;           // residual (iteration precision)
   cplx<R>* x;           // iterate accumulated between reliable updates
   cplx<LO>* lo_x;       // RU_P1: low-precision iterate folded in and zeroed
+  const cplx<LO>* lo_p; // RU_P1: search direction of the pending x update
   cplx<LO>* lo_r;       // RU_P5: residual written in the iteration precision
   const cplx<R>* b;     // RU_P5: right-hand side
   const cplx<R>* phi;
@@ -151,9 +154,8 @@ xy_cg(CGArgs<R, LO> a) {
     constexpr unsigned PB = L * L * 4 * sizeof(cplx<R>);
     const long pe = plane * (long)(L * L) * 4;
     if constexpr (MODE == CG_P5) {
-      prefetch_l2(Pp + pe, PB);
+      if (a.shift != 0.0) prefetch_l2(Pp + pe, PB);
       prefetch_l2(Pc + pe, PB);
-      prefetch_l2(Px + pe, PB);
       prefetch_l2(Pr + pe, PB);
     } else if constexpr (MODE == CG_P3) {
       prefetch_l2(Pp + pe, PB);
@@ -162,6 +164,7 @@ xy_cg(CGArgs<R, LO> a) {
       prefetch_l2(Pc + pe, PB);
       prefetch_l2(Pb + pe, PB);
     }
+    if constexpr (MODE == CG_P5) (void)Px;
   }
 
   if constexpr (MODE == CG_P5) {
@@ -177,7 +180,11 @@ xy_cg(CGArgs<R, LO> a) {
   }
   R alpha = R(0), beta = R(0);
   if constexpr (MODE == CG_P5) alpha = (R)red[32];
-  if constexpr (MODE == CG_P1) beta = (R)st->beta;
+  if constexpr (MODE == CG_P1) {
+    beta = (R)st->beta;
+    alpha = (R)st->alpha;  // pending x update of the previous iteration
+  }
+  const double alpha_pending = (MODE == RU_P1) ? st->alpha : 0.0;
   const R sigma = (R)a.shift;
 
   if (live) {
@@ -189,8 +196,13 @@ xy_cg(CGArgs<R, LO> a) {
     for (int y = 0; y < L; ++y) {
       const long e = (site0 + y * L) * 4 + s;
       if constexpr (MODE == CG_P1) {
-        // beta == 0 (first step): p = r without reading the previous p
-        const cplx<R> pv = beta != R(0) ? Pr[e] + beta * Pp[e] : Pr[e];
+        // beta == 0 and alpha == 0 (first step): p = r without reading the previous p
+        cplx<R> pv = Pr[e];
+        if (beta != R(0) || alpha != R(0)) {
+          const cplx<R> po = Pp[e];
+          if (alpha != R(0)) Px[e] = Px[e] + alpha * po;
+          pv = pv + beta * po;
+        }
         Pp[e] = pv;
         v[y] = pv;
       } else if constexpr (MODE == CG_P3) {
@@ -202,13 +214,11 @@ xy_cg(CGArgs<R, LO> a) {
         part += norm2(v[y]) + sigma * norm2(pe);
         if constexpr (PC) v[y] = site_coef<R, true, false>(a.k, f, s) * v[y];
       } else if constexpr (MODE == CG_P5 || MODE == RU_P5) {
-        const cplx<R> pe = Pp[e];  // p, or x_hi for RU_P5
         cplx<R> ap;
         if constexpr (PC) ap = Pc[e] + v[y];
         else ap = v[y] + site_coef<R, true, true>(a.k, a.phi[phib + y * L], s) * Pc[e];
-        ap = ap + sigma * pe;
+        if (sigma != R(0)) ap = ap + sigma * Pp[e];  // p, or x_hi for RU_P5
         if constexpr (MODE == CG_P5) {
-          Px[e] = Px[e] + alpha * pe;
           const cplx<R> rn = Pr[e] - alpha * ap;
           Pr[e] = rn;
           part += norm2(rn);
@@ -219,7 +229,8 @@ xy_cg(CGArgs<R, LO> a) {
         }
       } else if constexpr (MODE == RU_P1) {
         const cplx<LO> xl = Plx[e];
-        const cplx<R> xv = Pp[e] + cplx<R>{(R)xl.x, (R)xl.y};
+        const cplx<LO> pl = a.lo_p[e];
+        const cplx<R> xv = Pp[e] + cplx<R>{(R)xl.x, (R)xl.y} + (R)alpha_pending * cplx<R>{(R)pl.x, (R)pl.y};
         Pp[e] = xv;
         Plx[e] = cplx<LO>{LO(0), LO(0)};
         v[y] = xv;
@@ -268,6 +279,7 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
     s->rmax2 = t;
     s->rtrue2 = t;
     s->tol2 = tol2;
+    s->alpha = 0.0;
     s->iters = 0;
     s->ru_count = 0;
     s->ru = 0;
@@ -277,11 +289,15 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
   }
 }
 
-static __global__ void cg_scalar_iter(RhsState* st, const double* part, int nblk, double delta2, int maxiter) {
+static __global__ void cg_scalar_iter(RhsState* st, const double* part, const double* part_pAp, int nblk,
+                                      double delta2, int maxiter) {
   RhsState* s = st + blockIdx.x;
   if (!s->run) return;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
+  // the alpha P5 used (the same sum, in the same order): pending for the next P1
+  const double pAp = sum_partials(part_pAp + (long)blockIdx.x * nblk, nblk);
   if (threadIdx.x == 0) {
+    s->alpha = pAp > 0.0 ? s->rr / pAp : 0.0;
     s->iters += 1;
     s->beta = t / s->rr;
     s->rr_prev = s->rr;
@@ -301,6 +317,7 @@ static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, 
     s->ru = 0;
     s->ru_count += 1;
     s->rtrue2 = t;
+    s->alpha = 0.0;  // RU_P1 folded the pending update into x_hi
     if (t <= s->tol2 * s->bnorm2) {
       s->active = 0;
       s->run = 0;

@@ -190,6 +190,31 @@ int wz_md_integrate(wz_ctx* ctx, void* pi, const void* eta, int npf, const wz_hm
  * device with a Philox uniform; on rejection phi is restored.  Synchronous. */
 int wz_trajectory(wz_ctx* ctx, const wz_hmc_params* h, wz_traj_stats* st);
 
+/* ---- batches of independent lattices (replicas of uneven extent and coupling) ----
+ *
+ * A batch holds n lattices, each with its own dims, m, g and phi (e.g. the
+ * multicanonical replicas of Sec. 6 run side by side).  Lattices of equal
+ * extent share one set of momentum tables and are processed together: one
+ * launch per pass covers all right-hand sides of all lattices of that extent;
+ * groups of different extent run concurrently on their own streams.  Lattice
+ * i draws its HMC random numbers with the Philox key seed + i. */
+typedef struct wz_batch wz_batch;
+int wz_batch_create(const wz_params* params, int n, void* stream, wz_batch** out);
+int wz_batch_destroy(wz_batch* batch);
+const char* wz_batch_last_error(const wz_batch* batch);
+int wz_batch_size(const wz_batch* batch);     /* lattices */
+int wz_batch_groups(const wz_batch* batch);   /* extent groups */
+/* phi of lattice i (complex128, host or device) */
+int wz_batch_set_phi(wz_batch* batch, int i, const void* phi);
+int wz_batch_get_phi(wz_batch* batch, int i, void* phi);
+/* b[i], x[i]: nrhs complex128 fields of lattice i (host or device).  Solves
+ * (M_i^dag M_i) x = b for every lattice like wz_solve (no preconditioning);
+ * stats summed over the batch (iterations: maximum).  Synchronous. */
+int wz_batch_solve(wz_batch* batch, const void* const* b, void* const* x, int nrhs, double tol, int maxiter,
+                   unsigned flags, wz_solve_stats* stats);
+/* One HMC trajectory of every lattice (wz_trajectory); st: n entries. */
+int wz_batch_trajectory(wz_batch* batch, const wz_hmc_params* h, wz_traj_stats* st);
+
 /* (M^dagger M + shift) psi like wz_apply(WZ_OP_MDAGM), without allocating.
  * The paper has no counterpart: this serves callers that cannot allocate
  * device memory at call time (all memory handed to their own pool, a loop in

@@ -96,6 +96,16 @@ def _load():
                       ctypes.POINTER(WzSolveStats)], I),
         "wz_md_integrate": ([P, P, P, I, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
         "wz_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
+        "wz_batch_create": ([ctypes.POINTER(WzParams), I, P, ctypes.POINTER(P)], I),
+        "wz_batch_destroy": ([P], I),
+        "wz_batch_last_error": ([P], ctypes.c_char_p),
+        "wz_batch_size": ([P], I),
+        "wz_batch_groups": ([P], I),
+        "wz_batch_set_phi": ([P, I, P], I),
+        "wz_batch_get_phi": ([P, I, P], I),
+        "wz_batch_solve": ([P, ctypes.POINTER(P), ctypes.POINTER(P), I, D, I, ctypes.c_uint,
+                            ctypes.POINTER(WzSolveStats)], I),
+        "wz_batch_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
         "wz_probe_begin": ([I, I], I),
         "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
@@ -111,7 +121,9 @@ LIB = _load()
 
 EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply",
            "wz_solve", "wz_apply_mdagm_noalloc", "wz_get_phi", "wz_force", "wz_md_integrate",
-           "wz_trajectory", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
+           "wz_trajectory", "wz_batch_create", "wz_batch_destroy", "wz_batch_last_error", "wz_batch_size",
+           "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
+           "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
 def _is_torch(x):
@@ -314,3 +326,63 @@ class Lattice:
         if nrhs is None:
             nrhs = inp.numel() // (4 * int(np.prod(self.dims))) if _is_torch(inp) else inp.size // (4 * int(np.prod(self.dims)))
         return wz_apply(self.ctx, op, inp, out, nrhs, shift)
+
+
+def _bcheck(b, rc, ok=(WZ_OK,)):
+    if rc not in ok:
+        raise WzError(rc, LIB.wz_batch_last_error(b).decode() if b else "")
+    return rc
+
+
+class Batch:
+    """Independent lattices of uneven extent and coupling; forwards to wz_batch_*."""
+
+    def __init__(self, lattices):
+        """lattices: list of dicts with dims, m, g (and optionally r, M0, yukawa)."""
+        self.n = len(lattices)
+        self.dims = [tuple(int(d) for d in l["dims"]) for l in lattices]
+        arr = (WzParams * self.n)()
+        for i, l in enumerate(lattices):
+            arr[i] = make_params(l["dims"], l.get("m", 0.1), l.get("g", 0.1), l.get("r", 1.0), l.get("M0", 1.0),
+                                 l.get("yukawa", 2.0))
+        h = ctypes.c_void_p()
+        rc = LIB.wz_batch_create(arr, self.n, None, ctypes.byref(h))
+        if rc != WZ_OK:
+            raise WzError(rc, "wz_batch_create failed")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            LIB.wz_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def groups(self):
+        return LIB.wz_batch_groups(self.h)
+
+    def set_phi(self, i, phi):
+        return _bcheck(self.h, LIB.wz_batch_set_phi(self.h, int(i), field_ptr(phi, WZ_C128)[0]))
+
+    def get_phi(self, i, phi):
+        return _bcheck(self.h, LIB.wz_batch_get_phi(self.h, int(i), field_ptr(phi, WZ_C128)[0]))
+
+    def solve(self, bs, xs, nrhs, tol=1e-10, maxiter=100000, mixed=True):
+        pb = (ctypes.c_void_p * self.n)(*[field_ptr(b, WZ_C128)[0].value for b in bs])
+        px = (ctypes.c_void_p * self.n)(*[field_ptr(x, WZ_C128)[0].value for x in xs])
+        st = WzSolveStats()
+        rc = LIB.wz_batch_solve(self.h, pb, px, int(nrhs), float(tol), int(maxiter),
+                                WZ_SOLVE_MIXED if mixed else 0, ctypes.byref(st))
+        _bcheck(self.h, rc)
+        return st.as_dict()
+
+    def trajectory(self, **kw):
+        p = hmc_params(**kw)
+        st = (WzTrajStats * self.n)()
+        _bcheck(self.h, LIB.wz_batch_trajectory(self.h, ctypes.byref(p), st))
+        return [x.as_dict() for x in st]

@@ -14,7 +14,8 @@
 namespace wz {
 
 Probe g_probe;
-unsigned long long g_launches = 0;
+std::atomic<unsigned long long> g_launches{0};
+thread_local unsigned long long tl_launches = 0;
 
 int set_error(wz_ctx* c, int code, const std::string& msg) {
   if (c) c->err = msg;
@@ -179,7 +180,7 @@ static int build_tables(wz_ctx* c) {
   a.d2sVf = c->t32.d2sV;
   a.ksVf = c->t32.ksV;
   const int blocks = (int)((V + 255) / 256 < 1024 ? (V + 255) / 256 : 1024);
-  g_launches += 2;
+  count_launch(2);
   momentum_tables_kernel<<<blocks, 256, 0, c->stream>>>(a);
   WZ_CUDA_TRY(c, cudaGetLastError());
   axis_tables_kernel<<<1, 256, 0, c->stream>>>(c->T, c->Z, c->Y, c->X, c->t64.sinT, c->t32.sinT);
@@ -236,16 +237,34 @@ extern "C" {
 
 int wz_supported_extent(int n) { return extent_supported(n) ? 1 : 0; }
 
-int wz_create(const wz_params* p, void* stream, wz_ctx** out) {
-  if (!p || !out) return WZ_EINVAL;
+}  // extern "C"
+
+namespace wz {
+
+// Context over nm lattices of the same extent (members); member 0 is the
+// lattice of the single-lattice API.
+int create_ctx(const wz_params* ps, int nm, void* stream, wz_ctx** out) {
+  if (!ps || !out || nm < 1) return WZ_EINVAL;
   *out = nullptr;
+  const wz_params* p = ps;
   const int T = p->dims[0], Z = p->dims[1], Y = p->dims[2], X = p->dims[3];
   if (T <= 0 || Z <= 0 || Y <= 0 || X <= 0 || (T % 2) != 0) return WZ_EINVAL;
   if (X != Y || !extent_supported(X) || !zt_supported(Z, T)) return WZ_EUNSUPPORTED;
-  if (p->r <= 0.0) return WZ_EINVAL;
+  for (int i = 0; i < nm; ++i) {
+    if (ps[i].r <= 0.0) return WZ_EINVAL;
+    for (int d = 0; d < 4; ++d)
+      if (ps[i].dims[d] != p->dims[d]) return WZ_EINVAL;
+  }
   wz_ctx* c = new (std::nothrow) wz_ctx();
   if (!c) return WZ_ENOMEM;
   c->p = *p;
+  c->nm = nm;
+  c->mp.assign(ps, ps + nm);
+  const double m2 = p->m_re * p->m_re + p->m_im * p->m_im;
+  for (int i = 0; i < nm; ++i) {
+    c->same_mass &= (ps[i].m_re * ps[i].m_re + ps[i].m_im * ps[i].m_im) == m2;
+    c->same_mass &= ps[i].r == p->r && ps[i].M0 == p->M0;
+  }
   c->T = T;
   c->Z = Z;
   c->Y = Y;
@@ -259,14 +278,29 @@ int wz_create(const wz_params* p, void* stream, wz_ctx** out) {
   c->use_graphs = !(ng && ng[0] == '1');
   int rc = build_tables(c);
   if (rc == WZ_OK) {
-    cudaError_t e = cudaMalloc(&c->phi64, sizeof(cplx<double>) * c->V);
-    if (e == cudaSuccess) e = cudaMalloc(&c->phi32, sizeof(cplx<float>) * c->V);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->phi64, 0, sizeof(cplx<double>) * c->V, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->phi32, 0, sizeof(cplx<float>) * c->V, c->stream);
+    std::vector<SiteCoef<double>> kd(nm);
+    std::vector<SiteCoef<float>> kf(nm);
+    for (int i = 0; i < nm; ++i) {
+      kd[i] = site_coef_of<double>(ps[i]);
+      kf[i] = site_coef_of<float>(ps[i]);
+    }
+    const size_t nphi = (size_t)nm * c->V;
+    cudaError_t e = cudaMalloc(&c->phi64, sizeof(cplx<double>) * nphi);
+    if (e == cudaSuccess) e = cudaMalloc(&c->phi32, sizeof(cplx<float>) * nphi);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->phi64, 0, sizeof(cplx<double>) * nphi, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->phi32, 0, sizeof(cplx<float>) * nphi, c->stream);
+    if (e == cudaSuccess) e = cudaMalloc(&c->k64, sizeof(SiteCoef<double>) * nm);
+    if (e == cudaSuccess) e = cudaMalloc(&c->k32, sizeof(SiteCoef<float>) * nm);
+    if (e == cudaSuccess) e = cudaMemcpy(c->k64, kd.data(), sizeof(SiteCoef<double>) * nm, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(c->k32, kf.data(), sizeof(SiteCoef<float>) * nm, cudaMemcpyHostToDevice);
+    std::vector<int> ids(nm);
+    for (int i = 0; i < nm; ++i) ids[i] = i;
+    if (e == cudaSuccess) e = cudaMalloc(&c->mid, sizeof(int) * nm);
+    if (e == cudaSuccess) e = cudaMemcpy(c->mid, ids.data(), sizeof(int) * nm, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, WZ_PINNED_BYTES);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (e != cudaSuccess) rc = cuda_error(c, e, "wz_create");
+    if (e != cudaSuccess) rc = cuda_error(c, e, "create");
   }
   if (rc != WZ_OK) {
     wz_destroy(c);
@@ -276,6 +310,26 @@ int wz_create(const wz_params* p, void* stream, wz_ctx** out) {
   return WZ_OK;
 }
 
+// phi of member i (complex128 [T][Z][Y][X], host or device) -> FP64 and FP32 copies
+int set_member_phi(wz_ctx* c, int i, const void* phi) {
+  if (!c || !phi || i < 0 || i >= c->nm) return set_error(c, WZ_EINVAL, "set_phi: bad argument");
+  const size_t n = sizeof(cplx<double>) * c->V;
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(c->phi64 + (long)i * c->V, phi, n, cudaMemcpyDefault, c->stream));
+  count_launch();
+  phi_to_f32_kernel<<<(unsigned)((c->V + 255) / 256 < 2048 ? (c->V + 255) / 256 : 2048), 256, 0, c->stream>>>(
+      c->phi64 + (long)i * c->V, c->phi32 + (long)i * c->V, c->V);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  if (!is_device_pointer(phi)) WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->phi_set = true;
+  return WZ_OK;
+}
+
+}  // namespace wz
+
+extern "C" {
+
+int wz_create(const wz_params* p, void* stream, wz_ctx** out) { return create_ctx(p, 1, stream, out); }
+
 int wz_destroy(wz_ctx* c) {
   if (!c) return WZ_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
@@ -284,6 +338,9 @@ int wz_destroy(wz_ctx* c) {
   if (c->t32.block) cudaFree(c->t32.block);
   if (c->phi64) cudaFree(c->phi64);
   if (c->phi32) cudaFree(c->phi32);
+  if (c->k64) cudaFree(c->k64);
+  if (c->k32) cudaFree(c->k32);
+  if (c->mid) cudaFree(c->mid);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   for (auto& g : c->solver_graph) g.release();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
@@ -298,24 +355,16 @@ int wz_destroy(wz_ctx* c) {
 
 const char* wz_last_error(const wz_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
-int wz_set_phi(wz_ctx* c, const void* phi) {
-  if (!c || !phi) return set_error(c, WZ_EINVAL, "wz_set_phi: null pointer");
-  const size_t n = sizeof(cplx<double>) * c->V;
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(c->phi64, phi, n, cudaMemcpyDefault, c->stream));
-  ++g_launches;
-  phi_to_f32_kernel<<<(unsigned)((c->V + 255) / 256 < 2048 ? (c->V + 255) / 256 : 2048), 256, 0, c->stream>>>(
-      c->phi64, c->phi32, c->V);
-  WZ_CUDA_TRY(c, cudaGetLastError());
-  if (!is_device_pointer(phi)) WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  c->phi_set = true;
-  return WZ_OK;
-}
+int wz_set_phi(wz_ctx* c, const void* phi) { return set_member_phi(c, 0, phi); }
 
 int wz_apply(wz_ctx* c, int op, int dtype, const void* in, void* out, int nrhs, double shift) {
   if (!c) return WZ_EINVAL;
   if (!in || !out || nrhs < 0) return set_error(c, WZ_EINVAL, "wz_apply: bad argument");
   if (op < WZ_OP_M || op > WZ_OP_MTILDE_DAGM) return set_error(c, WZ_EINVAL, "wz_apply: unknown op");
   if (nrhs == 0) return WZ_OK;
+  if (c->nm > 1 && nrhs % c->nm) return set_error(c, WZ_EINVAL, "wz_apply: nrhs must be a multiple of the members");
+  if (!c->same_mass && op >= WZ_OP_M0INV && op != WZ_OP_DSLASH)
+    return set_error(c, WZ_EINVAL, "wz_apply: M0^-1 operators need one mass for all members");
   if (dtype == WZ_C128) return apply_typed<double>(c, op, in, out, nrhs, shift);
   if (dtype == WZ_C64) return apply_typed<float>(c, op, in, out, nrhs, shift);
   return set_error(c, WZ_EINVAL, "wz_apply: unknown dtype");
@@ -327,6 +376,7 @@ int wz_solve(wz_ctx* c, const void* b, void* x, int nrhs, double shift, double t
   if (!b || !x || nrhs < 0 || tol <= 0.0 || maxiter < 1 || shift < 0.0)
     return set_error(c, WZ_EINVAL, "wz_solve: bad argument");
   if (b == x) return set_error(c, WZ_EINVAL, "wz_solve: b and x must not alias");
+  if (c->nm > 1 && nrhs % c->nm) return set_error(c, WZ_EINVAL, "wz_solve: nrhs must be a multiple of the members");
   if ((flags & WZ_SOLVE_PC) && shift != 0.0)
     return set_error(c, WZ_EINVAL, "wz_solve: M0^-1 preconditioning is defined for shift = 0 only");
   const auto t0 = std::chrono::steady_clock::now();
@@ -348,6 +398,7 @@ int wz_solve(wz_ctx* c, const void* b, void* x, int nrhs, double shift, double t
     if (!dx) px = sb + 4L * c->V * nrhs;
   }
   const bool pc = (flags & WZ_SOLVE_PC) != 0;
+  if (pc && !c->same_mass) return set_error(c, WZ_EINVAL, "wz_solve: M0^-1 preconditioning needs one mass for all members");
   SolveOut o;
   int rc = (flags & WZ_SOLVE_MIXED) ? solve_impl<float>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.1, &o)
                                     : solve_impl<double>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.0, &o);
@@ -374,7 +425,7 @@ int wz_solve(wz_ctx* c, const void* b, void* x, int nrhs, double shift, double t
   return rc;
 }
 
-unsigned long long wz_kernel_launches(void) { return g_launches; }
+unsigned long long wz_kernel_launches(void) { return g_launches.load(); }
 
 int wz_probe_begin(int kind, int real_bytes) {
   Probe& p = g_probe;

@@ -124,19 +124,25 @@ static cudaError_t launch_zt(int nz, int nt, int mul, const ZTArgs<R>& a, int nr
   return cudaErrorInvalidValue;
 }
 
-template <typename R> static SiteCoef<R> site_coef_of(const wz_ctx* c) {
+template <typename R> static SiteCoef<R> site_coef_of(const wz_params& p) {
   SiteCoef<R> k;
-  k.m_re = (R)c->p.m_re;
-  k.m_im = (R)c->p.m_im;
-  k.cg_re = (R)(c->p.yukawa * c->p.g_re);
-  k.cg_im = (R)(c->p.yukawa * c->p.g_im);
+  k.m_re = (R)p.m_re;
+  k.m_im = (R)p.m_im;
+  k.cg_re = (R)(p.yukawa * p.g_re);
+  k.cg_im = (R)(p.yukawa * p.g_im);
+  k.g_re = (R)p.g_re;
+  k.g_im = (R)p.g_im;
   return k;
 }
+
+// right-hand sides per member for a launch over nrhs right-hand sides in total
+static inline int rhs_per_member(const wz_ctx* c, int nrhs) { return c->nm > 1 ? nrhs / c->nm : (nrhs > 0 ? nrhs : 1); }
 
 template <typename R> static XYArgs<R> xy_args(const wz_ctx* c, int nrhs) {
   XYArgs<R> a{};
   a.phi = phi_of<R>(c);
-  a.k = site_coef_of<R>(c);
+  a.kArr = karr_of<R>(c);
+  a.rpm = rhs_per_member(c, nrhs);
   a.nplanes = nrhs * c->T * c->Z;
   a.TZ = c->T * c->Z;
   return a;

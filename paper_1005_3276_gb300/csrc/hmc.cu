@@ -30,7 +30,7 @@ static cudaError_t launch_fk_L(int which, const ForceArgs<double>& a, dim3 grid,
     if (e != cudaSuccess) return e;
     done[which] = true;
   }
-  ++g_launches;
+  count_launch();
   if (which == FK_FORCE) xy_force<L><<<grid, S::THREADS, smem, st>>>(a);
   if (which == FK_BOSON_FWD) xy_boson_fwd<L><<<grid, S::THREADS, smem, st>>>(a);
   if (which == FK_BOSON_INV) xy_boson_inv<L><<<grid, S::THREADS, smem, st>>>(a);
@@ -62,41 +62,45 @@ static unsigned grid1d(long n) {
   return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
 }
 
-// Workspace of the force / MD code (FP64), carved from ctx->ws_force.
+// Workspace of the force / MD code (FP64), carved from ctx->ws_force.  Every
+// field carries the member index outermost; npf pseudofermions per member.
 struct ForceWS {
-  cplx<double>* X;     // [npf][V][4] solutions
-  cplx<double>* A;     // [npf][V][4] momentum intermediate
-  cplx<double>* Gk;    // [npf][V] per-pseudofermion forces
-  cplx<double>* Bk;    // [V][4] packed scalar field / its transform
-  cplx<double>* G;     // [V] total force
-  cplx<double>* pi;    // [V] momenta
-  cplx<double>* phi0;  // [V] phi at the start of the trajectory
-  cplx<double>* R;     // [npf][V][4] heatbath sources
-  cplx<double>* eta;   // [npf][V][4] pseudofermions
-  double* sb0;         // S_B partials at the start
-  double* sb1;         // S_B partials of the latest force evaluation
-  double* kin0;        // |pi|^2 partials at the start
+  cplx<double>* X;     // [nm][npf][V][4] solutions
+  cplx<double>* A;     // [nm][npf][V][4] momentum intermediate
+  cplx<double>* Gk;    // [nm][npf][V] per-pseudofermion forces
+  cplx<double>* Bk;    // [nm][V][4] packed scalar field / its transform
+  cplx<double>* G;     // [nm][V] total force
+  cplx<double>* pi;    // [nm][V] momenta
+  cplx<double>* phi0;  // [nm][V] phi at the start of the trajectory
+  cplx<double>* R;     // [nm][npf][V][4] heatbath sources
+  cplx<double>* eta;   // [nm][npf][V][4] pseudofermions
+  double* sb0;         // [nm][nb] S_B partials at the start
+  double* sb1;         // [nm][nb] S_B partials of the latest force evaluation
+  double* kin0;        // [nm][ND] |pi|^2 partials at the start
   double* kin1;
-  double* spf0;        // |R|^2 partials
-  double* spf1;        // Re eta^dag X partials
-  double* res;         // metropolis result [H0, H1, dH, u, accept]
+  double* spf0;        // [nm][ND] |R|^2 partials
+  double* spf1;        // [nm][ND] Re eta^dag X partials
+  double* res;         // [nm][5] metropolis results [H0, H1, dH, u, accept]
   int nb;              // xy blocks for one field
 };
 
-static const int NPART = 4096;  // partial arrays are sized for the largest grid used
+static const int ND = 128;  // blocks of the dot-product partials per member
 
 static int force_ws(wz_ctx* c, int npf, ForceWS* w) {
+  const long nm = c->nm;
   const size_t f4 = sizeof(cplx<double>) * 4 * (size_t)c->V;
   const size_t f1 = sizeof(cplx<double>) * (size_t)c->V;
+  w->nb = xy_blocks(c->X, c->T * c->Z);
+  const size_t npart = (size_t)nm * (w->nb > ND ? w->nb : ND);
   size_t off = 0;
   auto take = [&](size_t n) {
     size_t r = off;
     off += (n + 255) & ~size_t(255);
     return r;
   };
-  const size_t oX = take(f4 * npf), oA = take(f4 * npf), oGk = take(f1 * npf), oB = take(f4), oG = take(f1),
-               oPi = take(f1), oP0 = take(f1), oR = take(f4 * npf), oE = take(f4 * npf),
-               oParts = take(sizeof(double) * (6 * NPART + 8));
+  const size_t oX = take(f4 * npf * nm), oA = take(f4 * npf * nm), oGk = take(f1 * npf * nm), oB = take(f4 * nm),
+               oG = take(f1 * nm), oPi = take(f1 * nm), oP0 = take(f1 * nm), oR = take(f4 * npf * nm),
+               oE = take(f4 * npf * nm), oParts = take(sizeof(double) * (6 * npart + 5 * nm + 8));
   WZ_CUDA_TRY(c, c->ws_force.reserve(off));
   char* b = (char*)c->ws_force.ptr;
   w->X = (cplx<double>*)(b + oX);
@@ -110,14 +114,12 @@ static int force_ws(wz_ctx* c, int npf, ForceWS* w) {
   w->eta = (cplx<double>*)(b + oE);
   double* p = (double*)(b + oParts);
   w->sb0 = p;
-  w->sb1 = p + NPART;
-  w->kin0 = p + 2 * NPART;
-  w->kin1 = p + 3 * NPART;
-  w->spf0 = p + 4 * NPART;
-  w->spf1 = p + 5 * NPART;
-  w->res = p + 6 * NPART;
-  w->nb = xy_blocks(c->X, c->T * c->Z);
-  if (w->nb > NPART) return set_error(c, WZ_EINVAL, "lattice too large for the force partials");
+  w->sb1 = p + npart;
+  w->kin0 = p + 2 * npart;
+  w->kin1 = p + 3 * npart;
+  w->spf0 = p + 4 * npart;
+  w->spf1 = p + 5 * npart;
+  w->res = p + 6 * npart;
   return WZ_OK;
 }
 
@@ -129,53 +131,52 @@ struct ForceOpts {
   bool boson = true;
 };
 
-// G = dS/dphi for the current phi; S_B partials into sb_part (nb values).
-// On return X holds (M^dag M)^-1 eta.
+// G = dS/dphi for the current phi of every member; S_B partials into
+// sb_part ([nm][nb]).  On return X holds (M^dag M)^-1 eta.
 static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int npf, const ForceOpts& o,
                       double* sb_part, SolveOut* so) {
   cudaStream_t s = c->stream;
   const int L = c->X;
   const int TZ = c->T * c->Z;
+  const int nm = c->nm;
   cudaError_t e;
   int npf_eff = o.fermion ? npf : 0;
   if (npf_eff > 0) {
-    int rc = o.mixed ? solve_impl<float>(c, eta, w.X, npf, 0.0, o.tol, o.maxiter, false, 0.1, so)
-                     : solve_impl<double>(c, eta, w.X, npf, 0.0, o.tol, o.maxiter, false, 0.0, so);
+    const int nr = nm * npf;  // right-hand sides of the batched solve
+    int rc = o.mixed ? solve_impl<float>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.1, so)
+                     : solve_impl<double>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.0, so);
     if (rc) return rc;
     // Z = M X without the site term: forward xy, +Dslash; the site term and the
     // contraction are fused into xy_force
-    XYArgs<double> xa{};
-    xa.phi = c->phi64;
-    xa.k = site_coef_of<double>(c);
-    xa.nplanes = npf * TZ;
-    xa.TZ = TZ;
+    XYArgs<double> xa = xy_args<double>(c, nr);
     xa.psi = w.X;
     xa.A_out = w.A;
     e = launch_xy<double>(L, XY_FWD, xa, s);
     if (e != cudaSuccess) return cuda_error(c, e, "force: xy forward");
     ZTArgs<double> za = zt_args<double>(c, 1.0);
     za.A = w.A;
-    e = launch_zt<double>(c->Z, c->T, ZT_DSLASH, za, npf, s);
+    e = launch_zt<double>(c->Z, c->T, ZT_DSLASH, za, nr, s);
     if (e != cudaSuccess) return cuda_error(c, e, "force: zt");
     ForceArgs<double> fa{};
     fa.A = w.A;
     fa.X = w.X;
     fa.Gk = w.Gk;
     fa.phi = c->phi64;
-    fa.k = site_coef_of<double>(c);
+    fa.kArr = c->k64;
+    fa.rpm = npf;
     fa.TZ = TZ;
     fa.V = c->V;
-    e = launch_fk(L, FK_FORCE, fa, dim3(w.nb, npf), s);
+    e = launch_fk(L, FK_FORCE, fa, dim3(w.nb, nr), s);
     if (e != cudaSuccess) return cuda_error(c, e, "force: xy_force");
   }
-  // bosonic part (+ the sum of the fermion forces)
+  // bosonic part (+ the sum of the fermion forces of each member)
   ForceArgs<double> ba{};
   ba.phi = c->phi64;
-  ba.k = site_coef_of<double>(c);  // the boson kernels use k.m; W' uses g itself
-  ba.g_re = c->p.g_re;
-  ba.g_im = c->p.g_im;
+  ba.kArr = c->k64;
+  ba.rpm = 1;
   ba.TZ = TZ;
   ba.V = c->V;
+  ba.nblk = w.nb;
   ba.A_out = w.Bk;
   ba.A = w.Bk;
   ba.Gk_in = w.Gk;
@@ -183,18 +184,18 @@ static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int 
   ba.G = w.G;
   ba.part = sb_part;
   if (o.boson) {
-    e = launch_fk(L, FK_BOSON_FWD, ba, dim3(w.nb), s);
+    e = launch_fk(L, FK_BOSON_FWD, ba, dim3(w.nb, nm), s);
     if (e != cudaSuccess) return cuda_error(c, e, "force: boson forward");
     ZTArgs<double> za = zt_args<double>(c, 1.0);
     za.A = w.Bk;
-    e = launch_zt<double>(c->Z, c->T, ZT_SCALAR, za, 1, s);
+    e = launch_zt<double>(c->Z, c->T, ZT_SCALAR, za, nm, s);
     if (e != cudaSuccess) return cuda_error(c, e, "force: boson zt");
   } else {
     // zero scalar transform: the inverse pass then only sums the fermion forces
-    e = cudaMemsetAsync(w.Bk, 0, sizeof(cplx<double>) * 4 * c->V, s);
+    e = cudaMemsetAsync(w.Bk, 0, sizeof(cplx<double>) * 4 * c->V * nm, s);
     if (e != cudaSuccess) return cuda_error(c, e, "force: memset");
   }
-  e = launch_fk(L, FK_BOSON_INV, ba, dim3(w.nb), s);
+  e = launch_fk(L, FK_BOSON_INV, ba, dim3(w.nb, nm), s);
   if (e != cudaSuccess) return cuda_error(c, e, "force: boson inverse");
   return WZ_OK;
 }
@@ -220,7 +221,7 @@ static void add_solve(SolveOut& acc, const SolveOut& s) {
 static int md_integrate(wz_ctx* c, ForceWS& w, const cplx<double>* eta, int npf, double tau, int nsteps,
                         int integrator, const ForceOpts& o, SolveOut* acc, int* nforce, bool first_into_sb0) {
   cudaStream_t s = c->stream;
-  const long V = c->V;
+  const long V = c->V * c->nm;  // all members' fields update together
   const double eps = tau / nsteps;
   const unsigned g = grid1d(V);
   SolveOut so;
@@ -234,12 +235,12 @@ static int md_integrate(wz_ctx* c, ForceWS& w, const cplx<double>* eta, int npf,
     return r;
   };
   auto P = [&](double h) {
-    g_launches++;
+    count_launch();
     update_pi<<<g, 256, 0, s>>>(w.pi, w.G, h, V);
     return cudaGetLastError();
   };
   auto Q = [&](double h) {
-    g_launches++;
+    count_launch();
     update_phi<<<g, 256, 0, s>>>(c->phi64, c->phi32, w.pi, h, V);
     return cudaGetLastError();
   };
@@ -268,6 +269,127 @@ static int md_integrate(wz_ctx* c, ForceWS& w, const cplx<double>* eta, int npf,
   return WZ_OK;
 }
 
+// sum of the per-member partial slices [nm][n] -> out[nm] (synchronises)
+static int host_member_sums(wz_ctx* c, const double* dev, int n, std::vector<double>& out) {
+  const int nm = c->nm;
+  double* pin = (double*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
+  if (sizeof(double) * (size_t)n * nm > WZ_PINNED_BYTES - WZ_PINNED_SCRATCH_OFFSET)
+    return set_error(c, WZ_EINVAL, "too many members for the pinned read-back");
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(pin, dev, sizeof(double) * n * nm, cudaMemcpyDeviceToHost, c->stream));
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  out.assign(nm, 0.0);
+  for (int j = 0; j < nm; ++j)
+    for (int i = 0; i < n; ++i) out[j] += pin[(long)j * n + i];
+  return WZ_OK;
+}
+
+// Forces and actions of every member.  eta: [nm][npf] fields (device).
+int force_impl(wz_ctx* c, const cplx<double>* eta, int npf, double tol, unsigned parts, cplx<double>* grad,
+               double* S_B, double* S_pf, SolveOut* so) {
+  ForceWS w;
+  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
+  if (rc) return rc;
+  ForceOpts o;
+  o.tol = tol;
+  o.fermion = (parts & 1) != 0 && npf > 0;
+  o.boson = (parts & 2) != 0;
+  rc = force_eval(c, w, eta, npf, o, w.sb1, so);
+  if (rc && rc != WZ_NOT_CONVERGED) return rc;
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(grad, w.G, sizeof(cplx<double>) * c->V * c->nm, cudaMemcpyDefault, c->stream));
+  std::vector<double> v;
+  if (S_B) {
+    if (o.boson) {
+      int r2 = host_member_sums(c, w.sb1, w.nb, v);
+      if (r2) return r2;
+      for (int j = 0; j < c->nm; ++j) S_B[j] = v[j];
+    } else {
+      for (int j = 0; j < c->nm; ++j) S_B[j] = 0.0;
+    }
+  }
+  if (S_pf) {
+    if (o.fermion) {
+      count_launch();
+      dot_re_partials<<<dim3(ND, c->nm), 256, 0, c->stream>>>(eta, w.X, 4L * c->V * npf, w.spf1);
+      WZ_CUDA_TRY(c, cudaGetLastError());
+      int r2 = host_member_sums(c, w.spf1, ND, v);
+      if (r2) return r2;
+      for (int j = 0; j < c->nm; ++j) S_pf[j] = v[j];
+    } else {
+      for (int j = 0; j < c->nm; ++j) S_pf[j] = 0.0;
+    }
+  }
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return rc;
+}
+
+// One trajectory of every member (Sec. 7.2); st: nm entries (may be null).
+int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int npf = h->npf;
+  const int nm = c->nm;
+  ForceWS w;
+  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
+  if (rc) return rc;
+  cudaStream_t s = c->stream;
+  const long V = c->V, VN = c->V * nm;
+  const unsigned g = grid1d(VN);
+  // heatbath: pi ~ N(0,1), R ~ exp(-|R|^2), eta = M^dag R
+  count_launch(2);
+  draw_momenta<<<g, 256, 0, s>>>(w.pi, V, nm, c->mid, h->seed, h->traj_index);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  if (npf > 0) {
+    draw_sources<<<grid1d(4 * VN * npf), 256, 0, s>>>(w.R, npf, V, nm, c->mid, h->seed, h->traj_index);
+    WZ_CUDA_TRY(c, cudaGetLastError());
+    WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAG, npf * nm)));
+    rc = apply_op<double>(c, WZ_OP_MDAG, w.R, w.eta, npf * nm, 0.0, (cplx<double>*)c->ws_apply.ptr);
+    if (rc) return rc;
+  }
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(w.phi0, c->phi64, sizeof(cplx<double>) * VN, cudaMemcpyDeviceToDevice, s));
+  count_launch(2);
+  dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.pi, w.pi, V, w.kin0);
+  if (npf > 0) dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.R, w.R, 4L * V * npf, w.spf0);
+  else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf0, 0, ND * nm * sizeof(double), s));
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  ForceOpts o;
+  o.tol = h->tol;
+  o.maxiter = h->maxiter > 0 ? h->maxiter : 100000;
+  o.mixed = (h->flags & WZ_HMC_FP64_SOLVES) == 0;
+  SolveOut acc;
+  int nf = 0;
+  rc = md_integrate(c, w, w.eta, npf, h->tau, h->nsteps, h->integrator, o, &acc, &nf, true);
+  if (rc) return rc;
+  count_launch(2);
+  dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.pi, w.pi, V, w.kin1);
+  if (npf > 0) dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.eta, w.X, 4L * V * npf, w.spf1);
+  else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf1, 0, ND * nm * sizeof(double), s));
+  HParts hp{w.kin0, ND, w.sb0, w.nb, w.spf0, ND, w.kin1, ND, w.sb1, w.nb, w.spf1, ND};
+  count_launch(2);
+  metropolis<<<(nm + 31) / 32, 32, 0, s>>>(hp, w.res, nm, c->mid, h->seed, h->traj_index);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  if (!(h->flags & WZ_HMC_NO_METROPOLIS)) {
+    restore_phi<<<g, 256, 0, s>>>(c->phi64, c->phi32, w.phi0, w.res, V, nm);
+    WZ_CUDA_TRY(c, cudaGetLastError());
+  }
+  double* pin = (double*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
+  if (sizeof(double) * 5 * nm > WZ_PINNED_BYTES - WZ_PINNED_SCRATCH_OFFSET)
+    return set_error(c, WZ_EINVAL, "too many members");
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(pin, w.res, 5 * nm * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(s));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  for (int j = 0; st && j < nm; ++j) {
+    st[j].H0 = pin[5 * j + 0];
+    st[j].H1 = pin[5 * j + 1];
+    st[j].dH = pin[5 * j + 2];
+    st[j].u = pin[5 * j + 3];
+    st[j].accept = (h->flags & WZ_HMC_NO_METROPOLIS) ? 1 : (pin[5 * j + 4] != 0.0);
+    st[j].force_evals = nf;
+    st[j].cg_iterations = acc.total_iterations;  // all members together
+    st[j].reliable_updates = acc.reliable_updates;
+    st[j].seconds = secs;
+  }
+  return WZ_OK;
+}
+
 }  // namespace wz
 
 using namespace wz;
@@ -285,37 +407,18 @@ int wz_force(wz_ctx* c, const void* eta, int npf, double tol, unsigned parts, vo
              double* S_pf, wz_solve_stats* stats) {
   if (!c) return WZ_EINVAL;
   if (!grad || npf < 0 || (npf > 0 && !eta) || tol <= 0.0) return set_error(c, WZ_EINVAL, "wz_force: bad argument");
+  if (c->nm != 1) return set_error(c, WZ_EINVAL, "wz_force: single-lattice context expected");
   const auto t0 = std::chrono::steady_clock::now();
-  ForceWS w;
-  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
-  if (rc) return rc;
   const size_t f4 = sizeof(cplx<double>) * 4 * (size_t)c->V;
   const cplx<double>* e = (const cplx<double>*)eta;
   if (npf > 0 && !is_device_pointer(eta)) {
-    WZ_CUDA_TRY(c, cudaMemcpyAsync(w.eta, eta, f4 * npf, cudaMemcpyHostToDevice, c->stream));
-    e = w.eta;
+    WZ_CUDA_TRY(c, c->ws_stage.reserve(f4 * npf));
+    WZ_CUDA_TRY(c, cudaMemcpyAsync(c->ws_stage.ptr, eta, f4 * npf, cudaMemcpyHostToDevice, c->stream));
+    e = (const cplx<double>*)c->ws_stage.ptr;
   }
-  ForceOpts o;
-  o.tol = tol;
-  o.fermion = (parts & 1) != 0 && npf > 0;
-  o.boson = (parts & 2) != 0;
   SolveOut so;
-  rc = force_eval(c, w, e, npf, o, w.sb1, &so);
+  int rc = force_impl(c, e, npf, tol, parts, (cplx<double>*)grad, S_B, S_pf, &so);
   if (rc && rc != WZ_NOT_CONVERGED) return rc;
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(grad, w.G, sizeof(cplx<double>) * c->V, cudaMemcpyDefault, c->stream));
-  double* pin = (double*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
-  if (S_B) *S_B = o.boson ? host_sum(c, w.sb1, w.nb, pin) : 0.0;
-  if (S_pf) {
-    if (o.fermion) {
-      ++g_launches;
-      dot_re_partials<<<256, 256, 0, c->stream>>>(e, w.X, 4L * c->V * npf, w.spf1);
-      WZ_CUDA_TRY(c, cudaGetLastError());
-      *S_pf = host_sum(c, w.spf1, 256, pin);
-    } else {
-      *S_pf = 0.0;
-    }
-  }
-  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (stats) {
     stats->iterations = so.iterations;
     stats->total_iterations = so.total_iterations;
@@ -331,6 +434,7 @@ int wz_md_integrate(wz_ctx* c, void* pi, const void* eta, int npf, const wz_hmc_
   if (!c) return WZ_EINVAL;
   if (!pi || !h || npf < 0 || (npf > 0 && !eta) || h->nsteps < 1 || h->tol <= 0.0)
     return set_error(c, WZ_EINVAL, "wz_md_integrate: bad argument");
+  if (c->nm != 1) return set_error(c, WZ_EINVAL, "wz_md_integrate: single-lattice context expected");
   const auto t0 = std::chrono::steady_clock::now();
   ForceWS w;
   int rc = force_ws(c, npf > 0 ? npf : 1, &w);
@@ -362,66 +466,8 @@ int wz_trajectory(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
   if (!c) return WZ_EINVAL;
   if (!h || h->npf < 0 || h->nsteps < 1 || h->tol <= 0.0 || h->tau <= 0.0)
     return set_error(c, WZ_EINVAL, "wz_trajectory: bad argument");
-  const auto t0 = std::chrono::steady_clock::now();
-  const int npf = h->npf;
-  ForceWS w;
-  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
-  if (rc) return rc;
-  cudaStream_t s = c->stream;
-  const long V = c->V;
-  const unsigned g = grid1d(V);
-  // heatbath: pi ~ N(0,1), R ~ exp(-|R|^2), eta = M^dag R
-  g_launches += 2;
-  draw_momenta<<<g, 256, 0, s>>>(w.pi, V, h->seed, h->traj_index);
-  WZ_CUDA_TRY(c, cudaGetLastError());
-  if (npf > 0) {
-    draw_sources<<<grid1d(4 * V * npf), 256, 0, s>>>(w.R, npf, V, h->seed, h->traj_index);
-    WZ_CUDA_TRY(c, cudaGetLastError());
-    WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAG, npf)));
-    rc = apply_op<double>(c, WZ_OP_MDAG, w.R, w.eta, npf, 0.0, (cplx<double>*)c->ws_apply.ptr);
-    if (rc) return rc;
-  }
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(w.phi0, c->phi64, sizeof(cplx<double>) * V, cudaMemcpyDeviceToDevice, s));
-  g_launches += 2;
-  dot_re_partials<<<256, 256, 0, s>>>(w.pi, w.pi, V, w.kin0);
-  if (npf > 0) dot_re_partials<<<256, 256, 0, s>>>(w.R, w.R, 4L * V * npf, w.spf0);
-  else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf0, 0, 256 * sizeof(double), s));
-  WZ_CUDA_TRY(c, cudaGetLastError());
-  ForceOpts o;
-  o.tol = h->tol;
-  o.maxiter = h->maxiter > 0 ? h->maxiter : 100000;
-  o.mixed = (h->flags & WZ_HMC_FP64_SOLVES) == 0;
-  SolveOut acc;
-  int nf = 0;
-  rc = md_integrate(c, w, w.eta, npf, h->tau, h->nsteps, h->integrator, o, &acc, &nf, true);
-  if (rc) return rc;
-  g_launches += 2;
-  dot_re_partials<<<256, 256, 0, s>>>(w.pi, w.pi, V, w.kin1);
-  if (npf > 0) dot_re_partials<<<256, 256, 0, s>>>(w.eta, w.X, 4L * V * npf, w.spf1);
-  else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf1, 0, 256 * sizeof(double), s));
-  HParts hp{w.kin0, 256, w.sb0, w.nb, w.spf0, 256, w.kin1, 256, w.sb1, w.nb, w.spf1, 256};
-  g_launches += 2;
-  metropolis<<<1, 32, 0, s>>>(hp, w.res, h->seed, h->traj_index);
-  WZ_CUDA_TRY(c, cudaGetLastError());
-  if (!(h->flags & WZ_HMC_NO_METROPOLIS)) {
-    restore_phi<<<g, 256, 0, s>>>(c->phi64, c->phi32, w.phi0, w.res, V);
-    WZ_CUDA_TRY(c, cudaGetLastError());
-  }
-  double* pin = (double*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(pin, w.res, 5 * sizeof(double), cudaMemcpyDeviceToHost, s));
-  WZ_CUDA_TRY(c, cudaStreamSynchronize(s));
-  if (st) {
-    st->H0 = pin[0];
-    st->H1 = pin[1];
-    st->dH = pin[2];
-    st->u = pin[3];
-    st->accept = (h->flags & WZ_HMC_NO_METROPOLIS) ? 1 : (pin[4] != 0.0);
-    st->force_evals = nf;
-    st->cg_iterations = acc.total_iterations;
-    st->reliable_updates = acc.reliable_updates;
-    st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
-  return WZ_OK;
+  if (c->nm != 1) return set_error(c, WZ_EINVAL, "wz_trajectory: single-lattice context expected");
+  return trajectory_impl(c, h, st);
 }
 
 }  // extern "C"

@@ -36,7 +36,7 @@ int true_residuals(wz_ctx* c, const cplx<double>* b, const cplx<double>* x, int 
   if (sizeof(double) * 2 * nrhs > WZ_PINNED_BYTES - WZ_PINNED_SCRATCH_OFFSET)
     return set_error(c, WZ_EINVAL, "too many right-hand sides");
   WZ_CUDA_TRY(c, c->ws_red.reserve(sizeof(double) * 2 * nrhs));
-  ++g_launches;
+  count_launch();
   residual_norms_kernel<<<nrhs, 256, 0, c->stream>>>(b, Ax, 4L * c->V, (double*)c->ws_red.ptr);
   WZ_CUDA_TRY(c, cudaGetLastError());
   double* h = (double*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);  // not the solver-state region

@@ -148,7 +148,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   }
 
   WZ_CUDA_TRY(c, cudaMemsetAsync(xs, 0, W.field64, s));
-  g_launches += 2;
+  count_launch(2);
   cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, p, n_per_rhs, partR, 64);
   WZ_CUDA_TRY(c, cudaGetLastError());
   cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol);
@@ -165,7 +165,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   ga.r = r;
   ga.x = xlo;
   ga.phi = phi_of<RI>(c);
-  ga.k = site_coef_of<RI>(c);
+  ga.kArr = karr_of<RI>(c);
+  ga.rpm = rhs_per_member(c, nrhs);
   ga.shift = shift;
   ga.st = st;
   ga.nblk = nblk;
@@ -181,7 +182,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   ra.lo_r = r;
   ra.b = bs;
   ra.phi = c->phi64;
-  ra.k = site_coef_of<double>(c);
+  ra.kArr = c->k64;
+  ra.rpm = ga.rpm;
   ra.shift = shift;
   ra.st = st;
   ra.nblk = nblk;
@@ -230,7 +232,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       a5.part_in = part3;
       a5.part_out = part5;
       WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, q));
-      ++g_launches;
+      count_launch();
       cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter);
       WZ_Q(cudaGetLastError());
     }
@@ -241,7 +243,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     r3.Cb = C64;
     r3.p = xs;
     r3.phi = c->phi64;
-    r3.k = ra.k;
+    r3.kArr = c->k64;
+    r3.rpm = ga.rpm;
     r3.shift = shift;
     r3.st = st;
     r3.nblk = nblk;
@@ -252,7 +255,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     CGArgs<double, RI> r5 = ra;
     r5.part_out = partR;
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, q));
-    ++g_launches;
+    count_launch();
     cg_scalar_ru<<<nrhs, 32, 0, q>>>(st, partR, nblk, maxiter);
     WZ_Q(cudaGetLastError());
 #undef WZ_Q
@@ -294,15 +297,16 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       cudaGraph_t body = np.conditional.phGraph_out[0];
       WZ_CUDA_TRY(c, cudaStreamBeginCaptureToGraph(c->cap_stream, body, nullptr, nullptr, 0,
                                                    cudaStreamCaptureModeRelaxed));
-      const unsigned long long l0 = g_launches;
+      const unsigned long long l0 = tl_launches;
       cudaError_t ce = issue_chunk(c->cap_stream);
       if (ce == cudaSuccess) {
-        ++g_launches;
+        count_launch();
         cg_loop_cond<<<1, 32, 0, c->cap_stream>>>(h, st, nrhs, trips, max_chunks);
         ce = cudaGetLastError();
       }
-      G.body_launches = g_launches - l0;  // kernels per trip of the WHILE body
-      g_launches = l0;                    // capturing launches nothing
+      G.body_launches = tl_launches - l0;  // kernels per trip of the WHILE body
+      g_launches -= G.body_launches;       // capturing launches nothing
+      tl_launches = l0;
       cudaGraph_t captured = nullptr;
       cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &captured);
       if (ce != cudaSuccess) return cuda_error(c, ce, "solver graph capture");
@@ -324,7 +328,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     int* htrips = (int*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET - 64);
     WZ_RUN(cudaMemcpyAsync(htrips, trips, sizeof(int), cudaMemcpyDeviceToHost, s));
     WZ_RUN(cudaStreamSynchronize(s));
-    g_launches += (unsigned long long)(*htrips) * G.body_launches;
+    count_launch((unsigned long long)(*htrips) * G.body_launches);
   } else {
     for (int chunk = 0; chunk < max_chunks; ++chunk) {
       WZ_RUN(issue_chunk(s));

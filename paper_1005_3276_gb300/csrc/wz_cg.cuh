@@ -65,8 +65,9 @@ template <typename R, typename LO> struct CGArgs {
   const cplx<LO>* lo_p; // RU_P1: search direction of the pending x update
   cplx<LO>* lo_r;       // RU_P5: residual written in the iteration precision
   const cplx<R>* b;     // RU_P5: right-hand side
-  const cplx<R>* phi;
-  SiteCoef<R> k;
+  const cplx<R>* phi;    // [member][T][Z][Y][X]
+  const SiteCoef<R>* kArr;  // couplings per member
+  int rpm;              // right-hand sides per member
   double shift;
   RhsState* st;
   double* part_out;     // [rhs][nblk] block partials written by this pass (may be null)
@@ -190,7 +191,9 @@ xy_cg(CGArgs<R, LO> a) {
   if (live) {
     const int x = w;
     const long site0 = plane * (long)(L * L) + x;
-    const long phib = (long)plane_in * (L * L) + x;
+    const int member = rhs / a.rpm;
+    const long phib = ((long)member * a.TZ + plane_in) * (L * L) + x;
+    const SiteCoef<R> kc = a.kArr[member];
     if (INV) H::inv_y(P, w, s, v);
 #pragma unroll
     for (int y = 0; y < L; ++y) {
@@ -208,15 +211,15 @@ xy_cg(CGArgs<R, LO> a) {
       } else if constexpr (MODE == CG_P3) {
         const cplx<R> pe = Pp[e];
         const cplx<R> f = a.phi[phib + y * L];
-        if constexpr (PC) v[y] = pe + site_coef<R, false, false>(a.k, f, s) * v[y];
-        else v[y] = v[y] + site_coef<R, false, true>(a.k, f, s) * pe;
+        if constexpr (PC) v[y] = pe + site_coef<R, false, false>(kc, f, s) * v[y];
+        else v[y] = v[y] + site_coef<R, false, true>(kc, f, s) * pe;
         Pc[e] = v[y];
         part += norm2(v[y]) + sigma * norm2(pe);
-        if constexpr (PC) v[y] = site_coef<R, true, false>(a.k, f, s) * v[y];
+        if constexpr (PC) v[y] = site_coef<R, true, false>(kc, f, s) * v[y];
       } else if constexpr (MODE == CG_P5 || MODE == RU_P5) {
         cplx<R> ap;
         if constexpr (PC) ap = Pc[e] + v[y];
-        else ap = v[y] + site_coef<R, true, true>(a.k, a.phi[phib + y * L], s) * Pc[e];
+        else ap = v[y] + site_coef<R, true, true>(kc, a.phi[phib + y * L], s) * Pc[e];
         if (sigma != R(0)) ap = ap + sigma * Pp[e];  // p, or x_hi for RU_P5
         if constexpr (MODE == CG_P5) {
           const cplx<R> rn = Pr[e] - alpha * ap;

@@ -4,9 +4,10 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "../../include/wz.h"
-#include "wz_fft.cuh"
+#include "wz_kernels.cuh"
 
 namespace wz {
 
@@ -78,7 +79,13 @@ struct SolverGraph {
 }  // namespace wz
 
 struct wz_ctx {
-  wz_params p{};
+  wz_params p{};                 // member 0 (the lattice of a single-lattice context)
+  int nm = 1;                    // members: lattices of the same extent sharing the tables
+  std::vector<wz_params> mp;     // parameters per member
+  bool same_mass = true;         // all members share |m| (the M0^-1 tables depend on it)
+  wz::SiteCoef<double>* k64 = nullptr;  // couplings per member (device)
+  wz::SiteCoef<float>* k32 = nullptr;
+  int* mid = nullptr;            // Philox key offset of each member (device; 0..nm-1, batch: lattice index)
   int T = 0, Z = 0, Y = 0, X = 0;
   long V = 0;
   cudaStream_t stream = nullptr;
@@ -87,7 +94,7 @@ struct wz_ctx {
 
   wz::Tables<double> t64;
   wz::Tables<float> t32;
-  wz::cplx<double>* phi64 = nullptr;
+  wz::cplx<double>* phi64 = nullptr;  // [member][T][Z][Y][X]
   wz::cplx<float>* phi32 = nullptr;
   bool phi_set = false;
 
@@ -122,12 +129,17 @@ template <typename R> size_t apply_ws_bytes(const wz_ctx* c, int op, int nrhs);
 template <typename R> const Tables<R>& tables(const wz_ctx* c);
 template <> inline const Tables<double>& tables<double>(const wz_ctx* c) { return c->t64; }
 template <> inline const Tables<float>& tables<float>(const wz_ctx* c) { return c->t32; }
+template <typename R> const SiteCoef<R>* karr_of(const wz_ctx* c);
+template <> inline const SiteCoef<double>* karr_of<double>(const wz_ctx* c) { return c->k64; }
+template <> inline const SiteCoef<float>* karr_of<float>(const wz_ctx* c) { return c->k32; }
 template <typename R> const cplx<R>* phi_of(const wz_ctx* c);
 template <> inline const cplx<double>* phi_of<double>(const wz_ctx* c) { return c->phi64; }
 template <> inline const cplx<float>* phi_of<float>(const wz_ctx* c) { return c->phi32; }
 
 bool extent_supported(int n);
 bool zt_supported(int nz, int nt);
+int create_ctx(const wz_params* ps, int nm, void* stream, wz_ctx** out);
+int set_member_phi(wz_ctx* c, int i, const void* phi);
 
 }  // namespace wz
 

@@ -29,9 +29,9 @@ template <typename R> struct ForceArgs {
   int npf;
   cplx<R>* G;             // xy_boson_inv: total force [V] (may be null)
   double* part;           // xy_boson_inv: block partials of S_B
-  const cplx<R>* phi;
-  SiteCoef<R> k;          // m, c g
-  R g_re, g_im;           // g (superpotential W' = m phi + g phi^2)
+  const cplx<R>* phi;     // [member][V]
+  const SiteCoef<R>* kArr;  // couplings per member
+  int rpm;                // pseudofermions per member (xy_force)
   int TZ;
   int nblk;
   long V;
@@ -63,7 +63,9 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_force(ForceArgs<double
   if (live) H::inv_x(a.A + base, P, w, s, v);
   __syncthreads();
   if (live) H::inv_y(P, w, s, v);
-  const cplx<R> cg{a.k.cg_re, a.k.cg_im};
+  const int member = k / a.rpm;
+  const SiteCoef<R> kc = a.kArr[member];
+  const cplx<R> cg{kc.cg_re, kc.cg_im};
   // chirality weight: spins 2,3 (P_+) carry c g, spins 0,1 (P_-) carry c g^*
   const cplx<R> wgt = s >= 2 ? cg : conj(cg);
   const R sgn = s >= 2 ? R(1) : R(-1);
@@ -74,8 +76,8 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_force(ForceArgs<double
     if (live) {
       const long e = (plane * (long)(L * L) + y * L + w) * 4 + s;
       const cplx<R> x = a.X[e];
-      const cplx<R> f = a.phi[site];
-      const cplx<R> z = v[y] + site_coef<R, false, true>(a.k, f, s) * x;  // Z = M X
+      const cplx<R> f = a.phi[member * a.V + site];
+      const cplx<R> z = v[y] + site_coef<R, false, true>(kc, f, s) * x;  // Z = M X
       const cplx<R> zx = conj(z) * x;
       const cplx<R> t = wgt * zx;
       dr = -R(2) * t.x;        // -2 Re[w Z^* X]
@@ -96,17 +98,19 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_boson_fwd(ForceArgs<do
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
   const int tid = threadIdx.x, pl_local = tid / S::TPP, w = (tid / 4) % L, s = tid & 3;
+  const int member = blockIdx.y;
   const int plane_in = blockIdx.x * S::PPC + pl_local;
   const bool live = plane_in < a.TZ;
   cplx<R>* P = sm + pl_local * S::PLANE;
-  const long base = (long)plane_in * (L * L) * 4;
+  const long base = ((long)member * a.TZ + plane_in) * (L * L) * 4;
+  const SiteCoef<R> kc = a.kArr[member];
   cplx<R> v[L];
   if (live) {
 #pragma unroll
     for (int y = 0; y < L; ++y) {
-      const cplx<R> f = a.phi[(long)plane_in * (L * L) + y * L + w];
+      const cplx<R> f = a.phi[member * a.V + (long)plane_in * (L * L) + y * L + w];
       if (s == 0) v[y] = f;
-      else if (s == 1) v[y] = cplx<R>{a.k.m_re, a.k.m_im} * f + cplx<R>{a.g_re, a.g_im} * (f * f);
+      else if (s == 1) v[y] = cplx<R>{kc.m_re, kc.m_im} * f + cplx<R>{kc.g_re, kc.g_im} * (f * f);
       else v[y] = cplx<R>{0, 0};
     }
     H::fwd_y(v, P, w, s);
@@ -125,16 +129,18 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_boson_inv(ForceArgs<do
   double* red = reinterpret_cast<double*>(sm + S::PLANE * S::PPC);
   const int tid = threadIdx.x, pl_local = tid / S::TPP, w = (tid / 4) % L, s = tid & 3;
   const int lane = tid & 31;
+  const int member = blockIdx.y;
   const int plane_in = blockIdx.x * S::PPC + pl_local;
   const bool live = plane_in < a.TZ;
   cplx<R>* P = sm + pl_local * S::PLANE;
-  const long base = (long)plane_in * (L * L) * 4;
+  const long base = ((long)member * a.TZ + plane_in) * (L * L) * 4;
   cplx<R> v[L];
   if (live) H::inv_x(a.A + base, P, w, s, v);
   __syncthreads();
   if (live) H::inv_y(P, w, s, v);
   double part = 0.0;
-  const cplx<R> m{a.k.m_re, a.k.m_im}, g{a.g_re, a.g_im};
+  const SiteCoef<R> kc = a.kArr[member];
+  const cplx<R> m{kc.m_re, kc.m_im}, g{kc.g_re, kc.g_im};
 #pragma unroll
   for (int y = 0; y < L; ++y) {
     cplx<R> d2, kw;  // (D2 phi) from spin slot 0, (K W') from slot 1 of this site
@@ -143,18 +149,20 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_boson_inv(ForceArgs<do
     kw.x = __shfl_sync(0xffffffffu, v[y].x, (lane & ~3) | 1);
     kw.y = __shfl_sync(0xffffffffu, v[y].y, (lane & ~3) | 1);
     if (live && s == 0) {
-      const long site = (long)plane_in * (L * L) + y * L + w;
+      const long site = member * a.V + (long)plane_in * (L * L) + y * L + w;
       const cplx<R> f = a.phi[site];
       const cplx<R> W = m * f + g * (f * f);
       const cplx<R> dW = m + R(2) * (g * f);  // W'' = m + 2 g phi
       cplx<R> G = R(4) * d2 + R(2) * (conj(dW) * kw);
-      for (int j = 0; j < a.npf; ++j) G = G + a.Gk_in[(long)j * a.V + site];
+      // this member's pseudofermion forces, in a fixed order
+      const long gk0 = (long)member * a.npf * a.V + (site - member * a.V);
+      for (int j = 0; j < a.npf; ++j) G = G + a.Gk_in[gk0 + (long)j * a.V];
       if (a.G) a.G[site] = G;
       part += R(2) * re_conj_mul(d2, f) + re_conj_mul(kw, W);  // 2 Re[phi^* D2 phi] + Re[W'^* K W']
     }
   }
   const double t = block_sum(part, red);
-  if (tid == 0) a.part[blockIdx.x] = t;
+  if (tid == 0) a.part[(long)member * a.nblk + blockIdx.x] = t;
 }
 
 // ----------------------------------------------------------------------------- Philox4x32-10
@@ -197,35 +205,49 @@ __device__ __forceinline__ cplx<double> gauss_pair(Philox4 w) {
 
 enum { STREAM_MOMENTUM = 1, STREAM_PSEUDOFERMION = 2, STREAM_ACCEPT = 3 };
 
-// pi(x): Re, Im ~ N(0, 1); counter (site, 0, STREAM_MOMENTUM, traj)
-__global__ void draw_momenta(cplx<double>* pi, long V, unsigned long long seed, unsigned int traj) {
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x)
-    pi[i] = gauss_pair(philox4x32_10((unsigned)i, 0u, STREAM_MOMENTUM, traj, (unsigned)seed, (unsigned)(seed >> 32)));
+// A member draws with the key seed + id (id = the lattice's index in its
+// batch; 0 for a single lattice), so a batch reproduces every lattice's
+// draws whatever the grouping.
+__device__ __forceinline__ Philox4 member_draw(unsigned long long seed, int id, unsigned c0, unsigned c1,
+                                               unsigned c2, unsigned c3) {
+  const unsigned long long key = seed + (unsigned long long)id;
+  return philox4x32_10(c0, c1, c2, c3, (unsigned)key, (unsigned)(key >> 32));
 }
 
-// R_k(x, s): density exp(-|R|^2); counter (site, 4k + s, STREAM_PSEUDOFERMION, traj)
-__global__ void draw_sources(cplx<double>* R, int npf, long V, unsigned long long seed, unsigned int traj) {
-  const long n = (long)npf * V * 4;
+// pi(x): Re, Im ~ N(0, 1); counter (site, 0, STREAM_MOMENTUM, traj); fields [member][V]
+__global__ void draw_momenta(cplx<double>* pi, long V, int nm, const int* mid, unsigned long long seed,
+                             unsigned int traj) {
+  const long n = (long)nm * V;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+    pi[i] = gauss_pair(member_draw(seed, mid[i / V], (unsigned)(i % V), 0u, STREAM_MOMENTUM, traj));
+}
+
+// R_k(x, s): density exp(-|R|^2); counter (site, 4k + s, STREAM_PSEUDOFERMION, traj),
+// k the pseudofermion within its member; fields [member][npf][V][4]
+__global__ void draw_sources(cplx<double>* R, int npf, long V, int nm, const int* mid, unsigned long long seed,
+                             unsigned int traj) {
+  const long n = (long)nm * npf * V * 4;
   const double sc = 0.70710678118654752440;  // sqrt(1/2)
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
     const int s = (int)(i & 3);
     const long site = (i >> 2) % V;
-    const int k = (int)((i >> 2) / V);
-    const cplx<double> z = gauss_pair(
-        philox4x32_10((unsigned)site, (unsigned)(4 * k + s), STREAM_PSEUDOFERMION, traj, (unsigned)seed,
-                      (unsigned)(seed >> 32)));
+    const long kk = (i >> 2) / V;  // member * npf + k
+    const int member = (int)(kk / npf), k = (int)(kk % npf);
+    const cplx<double> z =
+        gauss_pair(member_draw(seed, mid[member], (unsigned)site, (unsigned)(4 * k + s), STREAM_PSEUDOFERMION, traj));
     R[i] = cplx<double>{sc * z.x, sc * z.y};
   }
 }
 
-// partials of sum Re[conj(a) b] over n complex values, grid (nblk)
+// partials of sum Re[conj(a) b] over n complex values per member, grid (nblk, members)
 __global__ void dot_re_partials(const cplx<double>* a, const cplx<double>* b, long n, double* part) {
   __shared__ double red[33];
+  const long off = (long)blockIdx.y * n;
   double t = 0.0;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-    t += re_conj_mul(a[i], b[i]);
+    t += re_conj_mul(a[off + i], b[off + i]);
   t = block_sum(t, red);
-  if (threadIdx.x == 0) part[blockIdx.x] = t;
+  if (threadIdx.x == 0) part[(long)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
 // phi += eps * pi (FP64 and its FP32 copy)
@@ -243,10 +265,10 @@ __global__ void update_pi(cplx<double>* pi, const cplx<double>* G, double eps, l
     pi[i] = pi[i] - eps * G[i];
 }
 
-// Metropolis on the device: sums the H partials in a fixed order, draws u and
-// decides.  out = [H0, H1, dH, u, accept]
+// Metropolis on the device, one thread per member: sums that member's H
+// partials in a fixed order, draws u and decides.  out[5 j ..] = [H0, H1, dH, u, accept]
 struct HParts {
-  const double* kin0; int nkin0;   // sum |pi|^2 at the start
+  const double* kin0; int nkin0;   // sum |pi|^2 at the start      ([member][n] each)
   const double* sb0; int nsb0;     // S_B at the start
   const double* spf0; int nspf0;   // sum |R|^2
   const double* kin1; int nkin1;
@@ -260,25 +282,31 @@ __device__ __forceinline__ double serial_sum(const double* p, int n) {
   return t;
 }
 
-__global__ void metropolis(HParts h, double* out, unsigned long long seed, unsigned int traj) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const double H0 = 0.5 * serial_sum(h.kin0, h.nkin0) + serial_sum(h.sb0, h.nsb0) + serial_sum(h.spf0, h.nspf0);
-  const double H1 = 0.5 * serial_sum(h.kin1, h.nkin1) + serial_sum(h.sb1, h.nsb1) + serial_sum(h.spf1, h.nspf1);
+__global__ void metropolis(HParts h, double* out, int nm, const int* mid, unsigned long long seed, unsigned int traj) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nm) return;
+  const double H0 = 0.5 * serial_sum(h.kin0 + (long)j * h.nkin0, h.nkin0) +
+                    serial_sum(h.sb0 + (long)j * h.nsb0, h.nsb0) + serial_sum(h.spf0 + (long)j * h.nspf0, h.nspf0);
+  const double H1 = 0.5 * serial_sum(h.kin1 + (long)j * h.nkin1, h.nkin1) +
+                    serial_sum(h.sb1 + (long)j * h.nsb1, h.nsb1) + serial_sum(h.spf1 + (long)j * h.nspf1, h.nspf1);
   const double dH = H1 - H0;
-  const Philox4 w = philox4x32_10(0u, 0u, STREAM_ACCEPT, traj, (unsigned)seed, (unsigned)(seed >> 32));
+  const Philox4 w = member_draw(seed, mid[j], 0u, 0u, STREAM_ACCEPT, traj);
   const double u = unit53(w.v[0], w.v[1]);
   const bool acc = dH <= 0.0 || u <= exp(-dH);
-  out[0] = H0;
-  out[1] = H1;
-  out[2] = dH;
-  out[3] = u;
-  out[4] = acc ? 1.0 : 0.0;
+  double* o = out + 5 * j;
+  o[0] = H0;
+  o[1] = H1;
+  o[2] = dH;
+  o[3] = u;
+  o[4] = acc ? 1.0 : 0.0;
 }
 
-// on rejection: phi = phi0 (FP64 and FP32 copies)
-__global__ void restore_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* phi0, const double* res, long V) {
-  if (res[4] != 0.0) return;
-  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
+// on rejection of member j: phi_j = phi0_j (FP64 and FP32 copies); fields [member][V]
+__global__ void restore_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* phi0, const double* res,
+                            long V, int nm) {
+  const long n = (long)nm * V;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    if (res[5 * (i / V) + 4] != 0.0) continue;
     phi[i] = phi0[i];
     phi32[i] = cplx<float>{(float)phi0[i].x, (float)phi0[i].y};
   }

@@ -34,7 +34,12 @@ namespace wz {
 template <typename R> struct SiteCoef {
   R m_re, m_im;    // bare mass m
   R cg_re, cg_im;  // c * g with c the Yukawa coefficient (2 in Eq. fmat)
+  R g_re, g_im;    // g itself (superpotential W' = m phi + g phi^2, Eq. acws)
 };
+
+// Members: a context can hold several lattices of the same extent (a batch of
+// replicas with their own phi, m and g).  Right-hand side j belongs to member
+// j / rpm; phi is stored [member][T][Z][Y][X] and kArr[member] holds the couplings.
 
 // coefficient multiplying spin component s at a site with field value f
 template <typename R, bool DAG, bool WITH_MASS>
@@ -71,8 +76,9 @@ template <typename R> struct XYArgs {
   const cplx<R>* psi;    // position-space operand of the site term
   const cplx<R>* psi2;   // + shift * psi2 (XY_INV_YDAG, XY_INV_ADD), may be null
   cplx<R>* v_out;        // position-space result of phase B
-  const cplx<R>* phi;    // scalar field [T][Z][Y][X]
-  SiteCoef<R> k;
+  const cplx<R>* phi;    // scalar fields [member][T][Z][Y][X]
+  const SiteCoef<R>* kArr;  // couplings per member
+  int rpm;               // right-hand sides per member
   R shift;
   int nplanes;           // nrhs * T * Z
   int TZ;                // planes per right-hand side
@@ -166,7 +172,9 @@ xy_pass(XYArgs<R> a) {
   if (live) {
     const int x = w;
     const long site0 = plane * (long)(L * L) + x;  // site index of (x, y=0)
-    const long phib = (plane % a.TZ) * (long)(L * L) + x;
+    const int member = (int)(plane / a.TZ) / a.rpm;
+    const long phib = ((long)member * a.TZ + plane % a.TZ) * (long)(L * L) + x;
+    const SiteCoef<R> kc = a.kArr[member];
     if (I::inv) {
 #pragma unroll
       for (int y = 0; y < L; ++y) v[y] = P[y * S::RP + x * 4 + s];
@@ -178,14 +186,14 @@ xy_pass(XYArgs<R> a) {
       if constexpr (MODE == XY_FWD) {
         v[y] = a.psi[e];
       } else if constexpr (MODE == XY_FWD_YINTDAG) {
-        v[y] = site_coef<R, true, false>(a.k, a.phi[phib + y * L], s) * a.psi[e];
+        v[y] = site_coef<R, true, false>(kc, a.phi[phib + y * L], s) * a.psi[e];
       } else if constexpr (MODE == XY_INV_Y || MODE == XY_INV_Y_FWD) {
-        v[y] = v[y] + site_coef<R, false, true>(a.k, a.phi[phib + y * L], s) * a.psi[e];
+        v[y] = v[y] + site_coef<R, false, true>(kc, a.phi[phib + y * L], s) * a.psi[e];
       } else if constexpr (MODE == XY_INV_YDAG) {
-        v[y] = v[y] + site_coef<R, true, true>(a.k, a.phi[phib + y * L], s) * a.psi[e];
+        v[y] = v[y] + site_coef<R, true, true>(kc, a.phi[phib + y * L], s) * a.psi[e];
         if (a.psi2) v[y] = v[y] + a.shift * a.psi2[e];
       } else if constexpr (MODE == XY_INV_PC || MODE == XY_INV_PC_FWD) {
-        v[y] = a.psi[e] + site_coef<R, false, false>(a.k, a.phi[phib + y * L], s) * v[y];
+        v[y] = a.psi[e] + site_coef<R, false, false>(kc, a.phi[phib + y * L], s) * v[y];
       } else if constexpr (MODE == XY_INV_ADD) {
         v[y] = a.psi[e] + v[y];
         if (a.psi2) v[y] = v[y] + a.shift * a.psi2[e];
@@ -194,7 +202,7 @@ xy_pass(XYArgs<R> a) {
         if (a.v_out) a.v_out[e] = v[y];
       }
       if constexpr (MODE == XY_INV_PC_FWD) {
-        v[y] = site_coef<R, true, false>(a.k, a.phi[phib + y * L], s) * v[y];
+        v[y] = site_coef<R, true, false>(kc, a.phi[phib + y * L], s) * v[y];
       }
     }
     if (I::fwd) {

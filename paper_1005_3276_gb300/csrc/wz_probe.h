@@ -9,6 +9,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <vector>
 
 namespace wz {
@@ -27,11 +28,17 @@ struct Probe {
 };
 
 extern Probe g_probe;
-extern unsigned long long g_launches;
+extern std::atomic<unsigned long long> g_launches;  // process-wide
+extern thread_local unsigned long long tl_launches;  // this host thread
+
+inline void count_launch(unsigned long long n = 1) {
+  g_launches += n;
+  tl_launches += n;
+}
 
 template <class F>
 inline cudaError_t probed(int kind, int real_bytes, double bytes_per_block, cudaStream_t st, F launch) {
-  ++g_launches;
+  count_launch();
   Probe& p = g_probe;
   const bool on = p.active && p.kind == kind && p.real_bytes == real_bytes;
   if (!on) return launch((unsigned long long*)nullptr);

@@ -299,6 +299,9 @@ int create_ctx(const wz_params* ps, int nm, void* stream, wz_ctx** out) {
     if (e == cudaSuccess) e = cudaMemcpy(c->mid, ids.data(), sizeof(int) * nm, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, WZ_PINNED_BYTES);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&c->counters, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, 4 * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) rc = cuda_error(c, e, "create");
   }
@@ -343,7 +346,10 @@ int wz_destroy(wz_ctx* c) {
   if (c->mid) cudaFree(c->mid);
   if (c->host_pinned) cudaFreeHost(c->host_pinned);
   for (auto& g : c->solver_graph) g.release();
+  c->traj_graph.release();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+  if (c->counters) cudaFree(c->counters);
   c->ws_apply.release();
   c->ws_stage.release();
   c->ws_solver.release();

@@ -9,8 +9,7 @@
 #include <cstring>
 #include <vector>
 
-#include "apply_impl.cuh"
-#include "solver.h"
+#include "solver_impl.cuh"
 #include "wz_hmc.cuh"
 
 namespace wz {
@@ -129,6 +128,7 @@ struct ForceOpts {
   bool mixed = true;
   bool fermion = true;
   bool boson = true;
+  bool inline_capture = false;  // solves become conditional nodes of an ongoing capture
 };
 
 // G = dS/dphi for the current phi of every member; S_B partials into
@@ -143,8 +143,8 @@ static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int 
   int npf_eff = o.fermion ? npf : 0;
   if (npf_eff > 0) {
     const int nr = nm * npf;  // right-hand sides of the batched solve
-    int rc = o.mixed ? solve_impl<float>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.1, so)
-                     : solve_impl<double>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.0, so);
+    int rc = o.mixed ? solve_impl<float>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.1, so, o.inline_capture)
+                     : solve_impl<double>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.0, so, o.inline_capture);
     if (rc) return rc;
     // Z = M X without the site term: forward xy, +Dslash; the site term and the
     // contraction are fused into xy_force
@@ -322,25 +322,25 @@ int force_impl(wz_ctx* c, const cplx<double>* eta, int npf, double tol, unsigned
   return rc;
 }
 
-// One trajectory of every member (Sec. 7.2); st: nm entries (may be null).
-int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
-  const auto t0 = std::chrono::steady_clock::now();
+// Enqueue one trajectory of every member (Sec. 7.2) on c->stream without any
+// host interaction in graph mode; the trajectory number is read on the device
+// from c->counters[3].  nf: force evaluations.
+static int enqueue_trajectory(wz_ctx* c, ForceWS& w, const wz_hmc_params* h, const ForceOpts& o, SolveOut* acc,
+                              int* nf) {
   const int npf = h->npf;
   const int nm = c->nm;
-  ForceWS w;
-  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
-  if (rc) return rc;
   cudaStream_t s = c->stream;
   const long V = c->V, VN = c->V * nm;
   const unsigned g = grid1d(VN);
+  const unsigned long long* trajp = c->counters + 3;
+  int rc;
   // heatbath: pi ~ N(0,1), R ~ exp(-|R|^2), eta = M^dag R
   count_launch(2);
-  draw_momenta<<<g, 256, 0, s>>>(w.pi, V, nm, c->mid, h->seed, h->traj_index);
+  draw_momenta<<<g, 256, 0, s>>>(w.pi, V, nm, c->mid, h->seed, trajp);
   WZ_CUDA_TRY(c, cudaGetLastError());
   if (npf > 0) {
-    draw_sources<<<grid1d(4 * VN * npf), 256, 0, s>>>(w.R, npf, V, nm, c->mid, h->seed, h->traj_index);
+    draw_sources<<<grid1d(4 * VN * npf), 256, 0, s>>>(w.R, npf, V, nm, c->mid, h->seed, trajp);
     WZ_CUDA_TRY(c, cudaGetLastError());
-    WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAG, npf * nm)));
     rc = apply_op<double>(c, WZ_OP_MDAG, w.R, w.eta, npf * nm, 0.0, (cplx<double>*)c->ws_apply.ptr);
     if (rc) return rc;
   }
@@ -350,13 +350,7 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
   if (npf > 0) dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.R, w.R, 4L * V * npf, w.spf0);
   else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf0, 0, ND * nm * sizeof(double), s));
   WZ_CUDA_TRY(c, cudaGetLastError());
-  ForceOpts o;
-  o.tol = h->tol;
-  o.maxiter = h->maxiter > 0 ? h->maxiter : 100000;
-  o.mixed = (h->flags & WZ_HMC_FP64_SOLVES) == 0;
-  SolveOut acc;
-  int nf = 0;
-  rc = md_integrate(c, w, w.eta, npf, h->tau, h->nsteps, h->integrator, o, &acc, &nf, true);
+  rc = md_integrate(c, w, w.eta, npf, h->tau, h->nsteps, h->integrator, o, acc, nf, true);
   if (rc) return rc;
   count_launch(2);
   dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.pi, w.pi, V, w.kin1);
@@ -364,27 +358,116 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
   else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf1, 0, ND * nm * sizeof(double), s));
   HParts hp{w.kin0, ND, w.sb0, w.nb, w.spf0, ND, w.kin1, ND, w.sb1, w.nb, w.spf1, ND};
   count_launch(2);
-  metropolis<<<(nm + 31) / 32, 32, 0, s>>>(hp, w.res, nm, c->mid, h->seed, h->traj_index);
+  metropolis<<<(nm + 31) / 32, 32, 0, s>>>(hp, w.res, nm, c->mid, h->seed, trajp);
   WZ_CUDA_TRY(c, cudaGetLastError());
   if (!(h->flags & WZ_HMC_NO_METROPOLIS)) {
     restore_phi<<<g, 256, 0, s>>>(c->phi64, c->phi32, w.phi0, w.res, V, nm);
     WZ_CUDA_TRY(c, cudaGetLastError());
   }
-  double* pin = (double*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
-  if (sizeof(double) * 5 * nm > WZ_PINNED_BYTES - WZ_PINNED_SCRATCH_OFFSET)
+  return WZ_OK;
+}
+
+// One trajectory of every member; st: nm entries (may be null).  In graph mode
+// the whole trajectory -- draws, heatbath, every force evaluation with its
+// solver loop as a WHILE conditional node, the updates, H and the Metropolis
+// decisions -- is one CUDA graph, captured once per parameter set and then
+// replayed (the trajectory number is written to the device before a replay).
+int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
+  const auto t0 = std::chrono::steady_clock::now();
+  const int npf = h->npf;
+  const int nm = c->nm;
+  ForceWS w;
+  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
+  if (rc) return rc;
+  if (npf > 0) WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAG, npf * nm)));
+  ForceOpts o;
+  o.tol = h->tol;
+  o.maxiter = h->maxiter > 0 ? h->maxiter : 100000;
+  o.mixed = (h->flags & WZ_HMC_FP64_SOLVES) == 0;
+  SolveOut acc;
+  int nf = 0;
+  cudaStream_t s = c->stream;
+  unsigned long long* hc = (unsigned long long*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
+  if (sizeof(double) * 5 * nm + 64 > WZ_PINNED_BYTES - WZ_PINNED_SCRATCH_OFFSET)
     return set_error(c, WZ_EINVAL, "too many members");
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(pin, w.res, 5 * nm * sizeof(double), cudaMemcpyDeviceToHost, s));
+  double* hres = (double*)(hc + 8);
+  // device state of this trajectory: counters zero, trajectory number
+  hc[0] = hc[1] = hc[2] = 0;
+  hc[3] = h->traj_index;
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(c->counters, hc, 4 * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+  const bool graph = c->use_graphs && !g_probe.active;
+  if (graph) {
+    // reserve the solver workspace now: nothing may allocate during the capture
+    {
+      const int nblk = xy_nblk(c->X, c->T * c->Z);
+      SolverWS<float> W1(c->V, nm * (npf > 0 ? npf : 1), nblk, false);
+      SolverWS<double> W2(c->V, nm * (npf > 0 ? npf : 1), nblk, false);
+      WZ_CUDA_TRY(c, c->ws_solver.reserve(o.mixed ? W1.total : W2.total));
+    }
+    TrajGraphKey key{};
+    key.tau = h->tau;
+    key.tol = h->tol;
+    key.nsteps = h->nsteps;
+    key.integrator = h->integrator;
+    key.npf = npf;
+    key.maxiter = o.maxiter;
+    key.flags = h->flags;
+    key.seed = h->seed;
+    key.ws_force = c->ws_force.ptr;
+    key.ws_solver = c->ws_solver.ptr;
+    key.ws_apply = c->ws_apply.ptr;
+    key.b_force = c->ws_force.bytes;
+    key.b_solver = c->ws_solver.bytes;
+    key.b_apply = c->ws_apply.bytes;
+    TrajGraph& T = c->traj_graph;
+    if (!T.exec || memcmp(&key, &T.key, sizeof(key)) != 0) {
+      T.release();
+      WZ_CUDA_TRY(c, cudaStreamSynchronize(s));
+      const unsigned long long l0 = tl_launches;
+      cudaStream_t saved = c->stream;
+      c->stream = c->cap_stream;
+      ForceOpts oc = o;
+      oc.inline_capture = true;
+      cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
+      int rc2 = e == cudaSuccess ? enqueue_trajectory(c, w, h, oc, &acc, &nf) : WZ_ECUDA;
+      cudaGraph_t gr = nullptr;
+      cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &gr);
+      c->stream = saved;
+      T.outer_launches = tl_launches - l0;
+      T.body_launches = c->inline_body_launches;
+      g_launches -= T.outer_launches;
+      tl_launches = l0;
+      if (e != cudaSuccess) return cuda_error(c, e, "trajectory capture");
+      if (rc2) {
+        if (gr) cudaGraphDestroy(gr);
+        return rc2;
+      }
+      if (ee != cudaSuccess) return cuda_error(c, ee, "trajectory cudaStreamEndCapture");
+      T.graph = gr;
+      WZ_CUDA_TRY(c, cudaGraphInstantiate(&T.exec, T.graph, 0));
+      T.force_evals = nf;
+      T.key = key;
+    }
+    WZ_CUDA_TRY(c, cudaGraphLaunch(T.exec, s));
+    nf = T.force_evals;
+  } else {
+    rc = enqueue_trajectory(c, w, h, o, &acc, &nf);
+    if (rc) return rc;
+  }
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(hres, w.res, 5 * nm * sizeof(double), cudaMemcpyDeviceToHost, s));
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(hc, c->counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   WZ_CUDA_TRY(c, cudaStreamSynchronize(s));
+  if (graph) count_launch(c->traj_graph.outer_launches + hc[2] * c->traj_graph.body_launches);
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int j = 0; st && j < nm; ++j) {
-    st[j].H0 = pin[5 * j + 0];
-    st[j].H1 = pin[5 * j + 1];
-    st[j].dH = pin[5 * j + 2];
-    st[j].u = pin[5 * j + 3];
-    st[j].accept = (h->flags & WZ_HMC_NO_METROPOLIS) ? 1 : (pin[5 * j + 4] != 0.0);
+    st[j].H0 = hres[5 * j + 0];
+    st[j].H1 = hres[5 * j + 1];
+    st[j].dH = hres[5 * j + 2];
+    st[j].u = hres[5 * j + 3];
+    st[j].accept = (h->flags & WZ_HMC_NO_METROPOLIS) ? 1 : (hres[5 * j + 4] != 0.0);
     st[j].force_evals = nf;
-    st[j].cg_iterations = acc.total_iterations;  // all members together
-    st[j].reliable_updates = acc.reliable_updates;
+    st[j].cg_iterations = (long long)hc[0];  // all members together
+    st[j].reliable_updates = (int)hc[1];
     st[j].seconds = secs;
   }
   return WZ_OK;

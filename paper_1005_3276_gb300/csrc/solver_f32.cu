@@ -2,5 +2,5 @@
 #include "solver_impl.cuh"
 namespace wz {
 template int solve_impl<float>(wz_ctx*, const cplx<double>*, cplx<double>*, int, double, double, int, bool, double,
-                               SolveOut*);
+                               SolveOut*, bool);
 }  // namespace wz

@@ -115,7 +115,8 @@ template <typename RI> struct SolverWS {
 // b, x: FP64 device fields.  RI: iteration precision (float: mixed, double: FP64).
 template <typename RI>
 int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, double shift, double tol, int maxiter,
-               bool pc, double delta, SolveOut* out) {
+               bool pc, double delta, SolveOut* out, bool inline_capture) {
+  if (inline_capture && pc) return set_error(c, WZ_EINVAL, "preconditioned solves cannot be captured inline");
   const int L = c->X;
   const int TZ = c->T * c->Z;
   const int nblk = xy_nblk(L, TZ);
@@ -233,7 +234,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       a5.part_out = part5;
       WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, q));
       count_launch();
-      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter);
+      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter, c->counters);
       WZ_Q(cudaGetLastError());
     }
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P1, ra, nrhs, q));
@@ -256,7 +257,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     r5.part_out = partR;
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, q));
     count_launch();
-    cg_scalar_ru<<<nrhs, 32, 0, q>>>(st, partR, nblk, maxiter);
+    cg_scalar_ru<<<nrhs, 32, 0, q>>>(st, partR, nblk, maxiter, c->counters);
     WZ_Q(cudaGetLastError());
 #undef WZ_Q
     return cudaSuccess;
@@ -271,6 +272,48 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   const bool use_graph = c->use_graphs && !g_probe.active;
   SolverGraph& G = c->solver_graph[sizeof(RI) == 4 ? 0 : 1];
   int* trips = (int*)(base + W.off_trips);
+
+  // Inline capture: the caller is capturing stream s into a larger graph (a
+  // whole HMC trajectory).  The chunk loop becomes a WHILE conditional node of
+  // that graph; its body is captured on a second stream.  No host interaction.
+  if (inline_capture) {
+    WZ_RUN(cudaMemsetAsync(trips, 0, sizeof(int), s));
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t capg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    WZ_RUN(cudaStreamGetCaptureInfo(s, &cs, nullptr, &capg, &deps, nullptr, &ndeps));
+    if (cs != cudaStreamCaptureStatusActive) return set_error(c, WZ_EINVAL, "inline solve outside a capture");
+    cudaGraphConditionalHandle h;
+    WZ_RUN(cudaGraphConditionalHandleCreate(&h, capg, 1, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    WZ_RUN(cudaGraphAddNode(&node, capg, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    WZ_RUN(cudaStreamBeginCaptureToGraph(c->cap_stream2, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed));
+    const unsigned long long l0 = tl_launches;
+    cudaError_t ce = issue_chunk(c->cap_stream2);
+    if (ce == cudaSuccess) {
+      count_launch();
+      cg_loop_cond<<<1, 32, 0, c->cap_stream2>>>(h, st, nrhs, trips, max_chunks, c->counters);
+      ce = cudaGetLastError();
+    }
+    c->inline_body_launches = tl_launches - l0;
+    g_launches -= c->inline_body_launches;
+    tl_launches = l0;
+    cudaGraph_t captured = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream2, &captured);
+    if (ce != cudaSuccess) return cuda_error(c, ce, "inline solver capture");
+    if (ee != cudaSuccess) return cuda_error(c, ee, "cudaStreamEndCapture (body)");
+    WZ_RUN(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    WZ_RUN(cudaMemcpyAsync(x, xs, W.field64, cudaMemcpyDeviceToDevice, s));
+    if (out) *out = SolveOut{};
+    return WZ_OK;
+  }
   if (use_graph) {
     SolverGraphKey key{};
     key.nrhs = nrhs;
@@ -301,7 +344,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       cudaError_t ce = issue_chunk(c->cap_stream);
       if (ce == cudaSuccess) {
         count_launch();
-        cg_loop_cond<<<1, 32, 0, c->cap_stream>>>(h, st, nrhs, trips, max_chunks);
+        cg_loop_cond<<<1, 32, 0, c->cap_stream>>>(h, st, nrhs, trips, max_chunks, c->counters);
         ce = cudaGetLastError();
       }
       G.body_launches = tl_launches - l0;  // kernels per trip of the WHILE body

@@ -292,8 +292,10 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
   }
 }
 
+// counters (may be null): [0] inner iterations summed over RHS, [1] reliable
+// updates, [2] trips of a solver graph's WHILE loop
 static __global__ void cg_scalar_iter(RhsState* st, const double* part, const double* part_pAp, int nblk,
-                                      double delta2, int maxiter) {
+                                      double delta2, int maxiter, unsigned long long* counters) {
   RhsState* s = st + blockIdx.x;
   if (!s->run) return;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
@@ -302,6 +304,7 @@ static __global__ void cg_scalar_iter(RhsState* st, const double* part, const do
   if (threadIdx.x == 0) {
     s->alpha = pAp > 0.0 ? s->rr / pAp : 0.0;
     s->iters += 1;
+    if (counters) atomicAdd(&counters[0], 1ULL);
     s->beta = t / s->rr;
     s->rr_prev = s->rr;
     s->rr = t;
@@ -312,13 +315,15 @@ static __global__ void cg_scalar_iter(RhsState* st, const double* part, const do
   }
 }
 
-static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, int maxiter) {
+static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, int maxiter,
+                                    unsigned long long* counters) {
   RhsState* s = st + blockIdx.x;
   if (!s->ru) return;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
   if (threadIdx.x == 0) {
     s->ru = 0;
     s->ru_count += 1;
+    if (counters) atomicAdd(&counters[1], 1ULL);
     s->rtrue2 = t;
     s->alpha = 0.0;  // RU_P1 folded the pending update into x_hi
     if (t <= s->tol2 * s->bnorm2) {
@@ -340,11 +345,13 @@ static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, 
 
 // Condition of the solver graph's WHILE node: continue while some RHS is
 // active, and never beyond cap trips.
-static __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const RhsState* st, int nrhs, int* trips, int cap) {
+static __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const RhsState* st, int nrhs, int* trips, int cap,
+                                    unsigned long long* counters) {
   if (threadIdx.x != 0) return;
   int any = 0;
   for (int j = 0; j < nrhs; ++j) any |= st[j].active;
   const int t = ++*trips;
+  if (counters) counters[2] += 1ULL;
   cudaGraphSetConditional(h, (any && t < cap) ? 1u : 0u);
 }
 

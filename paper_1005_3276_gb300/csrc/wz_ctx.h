@@ -76,6 +76,30 @@ struct SolverGraph {
   }
 };
 
+// Cached CUDA graph of a whole HMC trajectory and what it was captured for.
+struct TrajGraphKey {
+  double tau, tol;
+  int nsteps, integrator, npf, maxiter;
+  unsigned flags;
+  unsigned long long seed;
+  void *ws_force, *ws_solver, *ws_apply;
+  size_t b_force, b_solver, b_apply;
+};
+struct TrajGraph {
+  TrajGraphKey key{};
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long outer_launches = 0, body_launches = 0;
+  int force_evals = 0;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    key = TrajGraphKey{};
+  }
+};
+
 }  // namespace wz
 
 struct wz_ctx {
@@ -109,7 +133,11 @@ struct wz_ctx {
   // solver graphs (index 0: mixed FP32 iteration, 1: FP64) and their capture stream
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t cap_stream2 = nullptr;          // body of solver loops inside a trajectory capture
+  unsigned long long* counters = nullptr;      // device: iterations, reliable updates, loop trips, trajectory number
+  unsigned long long inline_body_launches = 0; // kernels per trip of an inline solver loop
   wz::SolverGraph solver_graph[2];
+  wz::TrajGraph traj_graph;
 };
 
 #define WZ_PINNED_BYTES (256 * 1024)

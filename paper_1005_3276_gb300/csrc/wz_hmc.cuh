@@ -215,8 +215,10 @@ __device__ __forceinline__ Philox4 member_draw(unsigned long long seed, int id, 
 }
 
 // pi(x): Re, Im ~ N(0, 1); counter (site, 0, STREAM_MOMENTUM, traj); fields [member][V]
+// traj: device word holding the trajectory number (the counter word c3)
 __global__ void draw_momenta(cplx<double>* pi, long V, int nm, const int* mid, unsigned long long seed,
-                             unsigned int traj) {
+                             const unsigned long long* trajp) {
+  const unsigned traj = (unsigned)*trajp;
   const long n = (long)nm * V;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
     pi[i] = gauss_pair(member_draw(seed, mid[i / V], (unsigned)(i % V), 0u, STREAM_MOMENTUM, traj));
@@ -225,7 +227,8 @@ __global__ void draw_momenta(cplx<double>* pi, long V, int nm, const int* mid, u
 // R_k(x, s): density exp(-|R|^2); counter (site, 4k + s, STREAM_PSEUDOFERMION, traj),
 // k the pseudofermion within its member; fields [member][npf][V][4]
 __global__ void draw_sources(cplx<double>* R, int npf, long V, int nm, const int* mid, unsigned long long seed,
-                             unsigned int traj) {
+                             const unsigned long long* trajp) {
+  const unsigned traj = (unsigned)*trajp;
   const long n = (long)nm * npf * V * 4;
   const double sc = 0.70710678118654752440;  // sqrt(1/2)
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -282,7 +285,9 @@ __device__ __forceinline__ double serial_sum(const double* p, int n) {
   return t;
 }
 
-__global__ void metropolis(HParts h, double* out, int nm, const int* mid, unsigned long long seed, unsigned int traj) {
+__global__ void metropolis(HParts h, double* out, int nm, const int* mid, unsigned long long seed,
+                           const unsigned long long* trajp) {
+  const unsigned traj = (unsigned)*trajp;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= nm) return;
   const double H0 = 0.5 * serial_sum(h.kin0 + (long)j * h.nkin0, h.nkin0) +

@@ -206,3 +206,25 @@ def test_autograd_function(wz):
     ref = oforce.pf_force(P, phi_np, eta_np[0], tol=1e-13)
     assert abs(float(S) - oforce.pf_action(P, phi_np, eta_np[0], tol=1e-13)) <= 1e-9 * abs(float(S))
     assert rel(phi.grad.cpu().numpy(), ref) <= 1e-8
+
+
+def test_trajectory_graph_equals_eager(wz, monkeypatch):
+    """Whole-trajectory CUDA graph (solver loops as conditional nodes) replayed
+    for three consecutive trajectories equals the eagerly launched sequence."""
+    dims = (8, 8, 8, 8)
+    phi0 = synth.scalar_field(dims, 0.5, 4)
+    runs = {}
+    for flag in ("0", "1"):
+        monkeypatch.setenv("WZ_NO_GRAPHS", flag)
+        lat = wz.Lattice(dims, m=0.2, g=0.4)
+        lat.set_phi(phi0)
+        out = []
+        for t in range(3):
+            st = lat.trajectory(tau=0.5, nsteps=5, npf=2, tol=1e-10, seed=5, traj_index=t)
+            out.append((st["dH"], st["accept"], st["cg_iterations"], st["force_evals"]))
+        phi = np.zeros(dims, np.complex128)
+        lat.get_phi(phi)
+        runs[flag] = (out, phi)
+        lat.close()
+    assert runs["0"][0] == runs["1"][0]
+    assert np.array_equal(runs["0"][1], runs["1"][1])

@@ -7,122 +7,10 @@
 //   M~ = 1 + Y_int M0^-1,  M~^dag = 1 + (M0^-1)^dag Y_int^dag   (Sec. 7.3, M0 M0^-1 = 1)
 #pragma once
 #include "wz_ctx.h"
-#include "wz_kernels.cuh"
-#include "wz_probe.h"
+#include "launch.h"
 
 namespace wz {
 
-// extents with compiled kernels; the xy pass needs X == Y, the zt pass a (Z, T) pair
-#define WZ_FOR_EXTENTS(F) F(4) F(6) F(8) F(12) F(16)
-#define WZ_FOR_ZT_PAIRS(F) F(4, 4) F(6, 6) F(8, 8) F(12, 12) F(16, 16) F(8, 16) F(16, 32) F(8, 32)
-
-template <typename Kern>
-static cudaError_t set_smem(Kern k, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
-  return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
-
-template <typename R, int L, int MODE>
-static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
-  using S = XYShape<L>;
-  const size_t smem = sizeof(cplx<R>) * S::PLANE * S::PPC;
-  static bool attr_done = false;  // one attribute call per instantiation and process
-  if (!attr_done) {
-    cudaError_t e = set_smem(xy_pass<R, L, MODE>, smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  const int grid = (a.nplanes + S::PPC - 1) / S::PPC;
-  if (grid == 0) return cudaSuccess;
-  // algorithmic bytes of one block: the spinor fields it reads and writes,
-  // plus phi where the site term needs it
-  using I = XYModeInfo<MODE>;
-  int fields = (I::inv ? 1 : 0) + (I::fwd ? 1 : 0) + (a.psi ? 1 : 0) + (a.psi2 ? 1 : 0) + (a.v_out ? 1 : 0);
-  const bool uses_phi = !(MODE == XY_FWD || MODE == XY_INV || MODE == XY_INV_ADD);
-  const double site = 4.0 * sizeof(cplx<R>) * fields + (uses_phi ? sizeof(cplx<R>) : 0);
-  const double blk_bytes = site * L * L * S::PPC;
-  return probed(PK_XY, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
-    XYArgs<R> b = a;
-    b.blk_count = cnt;
-    b.probe_inc = (unsigned long long)blk_bytes;
-    xy_pass<R, L, MODE><<<grid, S::THREADS, smem, st>>>(b);
-    return cudaGetLastError();
-  });
-}
-
-template <typename R, int L>
-static cudaError_t launch_xy_L(int mode, const XYArgs<R>& a, cudaStream_t st) {
-  switch (mode) {
-    case XY_FWD: return launch_xy_t<R, L, XY_FWD>(a, st);
-    case XY_FWD_YINTDAG: return launch_xy_t<R, L, XY_FWD_YINTDAG>(a, st);
-    case XY_INV: return launch_xy_t<R, L, XY_INV>(a, st);
-    case XY_INV_Y: return launch_xy_t<R, L, XY_INV_Y>(a, st);
-    case XY_INV_YDAG: return launch_xy_t<R, L, XY_INV_YDAG>(a, st);
-    case XY_INV_Y_FWD: return launch_xy_t<R, L, XY_INV_Y_FWD>(a, st);
-    case XY_INV_PC: return launch_xy_t<R, L, XY_INV_PC>(a, st);
-    case XY_INV_PC_FWD: return launch_xy_t<R, L, XY_INV_PC_FWD>(a, st);
-    case XY_INV_ADD: return launch_xy_t<R, L, XY_INV_ADD>(a, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename R>
-static cudaError_t launch_xy(int L, int mode, const XYArgs<R>& a, cudaStream_t st) {
-  switch (L) {
-#define WZ_CASE(n) \
-  case n: return launch_xy_L<R, n>(mode, a, st);
-    WZ_FOR_EXTENTS(WZ_CASE)
-#undef WZ_CASE
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename R, int NZ, int NT, int MUL>
-static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
-  using S = ZTShape<R, NZ, NT>;
-  constexpr int C = S::C;
-  const size_t smem = sizeof(cplx<R>) * NZ * NT * C * 4;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = set_smem(zt_pass<R, NZ, NT, MUL>, smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  const long grid = (long)nrhs * a.ntiles;
-  if (grid == 0) return cudaSuccess;
-  // one block reads and writes C columns x NZ x NT sites of 4 spins and reads
-  // the momentum tables it needs (1 for Dslash, 2 for M0^-1)
-  const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));  // ZT_SCALAR: 2 tables too
-  return probed(PK_ZT, (int)sizeof(R), bytes, st, [&](unsigned long long* cnt) {
-    ZTArgs<R> b = a;
-    b.blk_count = cnt;
-    b.probe_inc = (unsigned long long)bytes;
-    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b);
-    return cudaGetLastError();
-  });
-}
-
-template <typename R, int NZ, int NT>
-static cudaError_t launch_zt_p(int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
-  switch (mul) {
-    case ZT_DSLASH: return launch_zt_t<R, NZ, NT, ZT_DSLASH>(a, nrhs, st);
-    case ZT_M0INV: return launch_zt_t<R, NZ, NT, ZT_M0INV>(a, nrhs, st);
-    case ZT_M0INV_DAG: return launch_zt_t<R, NZ, NT, ZT_M0INV_DAG>(a, nrhs, st);
-    case ZT_SCALAR:
-      if constexpr (sizeof(R) == 8) return launch_zt_t<R, NZ, NT, ZT_SCALAR>(a, nrhs, st);
-      break;
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename R>
-static cudaError_t launch_zt(int nz, int nt, int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
-#define WZ_CASE(z, t) \
-  if (nz == z && nt == t) return launch_zt_p<R, z, t>(mul, a, nrhs, st);
-  WZ_FOR_ZT_PAIRS(WZ_CASE)
-#undef WZ_CASE
-  return cudaErrorInvalidValue;
-}
 
 template <typename R> static SiteCoef<R> site_coef_of(const wz_params& p) {
   SiteCoef<R> k;

@@ -14,48 +14,6 @@
 
 namespace wz {
 
-enum { FK_FORCE = 0, FK_BOSON_FWD = 1, FK_BOSON_INV = 2 };
-
-template <int L>
-static cudaError_t launch_fk_L(int which, const ForceArgs<double>& a, dim3 grid, cudaStream_t st) {
-  using S = XYShape<L>;
-  const size_t smem = sizeof(cplx<double>) * S::PLANE * S::PPC + 33 * sizeof(double);
-  static bool done[3] = {false, false, false};
-  cudaError_t e = cudaSuccess;
-  if (!done[which]) {
-    if (which == FK_FORCE) e = set_smem(xy_force<L>, smem);
-    if (which == FK_BOSON_FWD) e = set_smem(xy_boson_fwd<L>, smem);
-    if (which == FK_BOSON_INV) e = set_smem(xy_boson_inv<L>, smem);
-    if (e != cudaSuccess) return e;
-    done[which] = true;
-  }
-  count_launch();
-  if (which == FK_FORCE) xy_force<L><<<grid, S::THREADS, smem, st>>>(a);
-  if (which == FK_BOSON_FWD) xy_boson_fwd<L><<<grid, S::THREADS, smem, st>>>(a);
-  if (which == FK_BOSON_INV) xy_boson_inv<L><<<grid, S::THREADS, smem, st>>>(a);
-  return cudaGetLastError();
-}
-
-static cudaError_t launch_fk(int L, int which, const ForceArgs<double>& a, dim3 grid, cudaStream_t st) {
-  switch (L) {
-#define WZ_CASE(n) \
-  case n: return launch_fk_L<n>(which, a, grid, st);
-    WZ_FOR_EXTENTS(WZ_CASE)
-#undef WZ_CASE
-  }
-  return cudaErrorInvalidValue;
-}
-
-static int xy_blocks(int L, int TZ) {
-  switch (L) {
-#define WZ_CASE(n) \
-  case n: return (TZ + XYShape<n>::PPC - 1) / XYShape<n>::PPC;
-    WZ_FOR_EXTENTS(WZ_CASE)
-#undef WZ_CASE
-  }
-  return 0;
-}
-
 static unsigned grid1d(long n) {
   long b = (n + 255) / 256;
   return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
@@ -89,7 +47,7 @@ static int force_ws(wz_ctx* c, int npf, ForceWS* w) {
   const long nm = c->nm;
   const size_t f4 = sizeof(cplx<double>) * 4 * (size_t)c->V;
   const size_t f1 = sizeof(cplx<double>) * (size_t)c->V;
-  w->nb = xy_blocks(c->X, c->T * c->Z);
+  w->nb = xy_nblk(c->X, c->T * c->Z);
   const size_t npart = (size_t)nm * (w->nb > ND ? w->nb : ND);
   size_t off = 0;
   auto take = [&](size_t n) {

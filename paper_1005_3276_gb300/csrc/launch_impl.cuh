@@ -1,0 +1,161 @@
+// Launch wrappers of every kernel template: grid sizes, dynamic shared memory,
+// algorithmic bytes for the probe.  Included only by the kern_L*.cu and
+// zt_*.cu translation units, which instantiate them once per extent.
+#pragma once
+#include "launch.h"
+
+namespace wz {
+
+
+template <typename R, int L, int MODE>
+static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
+  using S = XYShape<L>;
+  const size_t smem = sizeof(cplx<R>) * S::PLANE * S::PPC;
+  static bool attr_done = false;  // one attribute call per instantiation and process
+  if (!attr_done) {
+    cudaError_t e = set_smem(xy_pass<R, L, MODE>, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const int grid = (a.nplanes + S::PPC - 1) / S::PPC;
+  if (grid == 0) return cudaSuccess;
+  // algorithmic bytes of one block: the spinor fields it reads and writes,
+  // plus phi where the site term needs it
+  using I = XYModeInfo<MODE>;
+  int fields = (I::inv ? 1 : 0) + (I::fwd ? 1 : 0) + (a.psi ? 1 : 0) + (a.psi2 ? 1 : 0) + (a.v_out ? 1 : 0);
+  const bool uses_phi = !(MODE == XY_FWD || MODE == XY_INV || MODE == XY_INV_ADD);
+  const double site = 4.0 * sizeof(cplx<R>) * fields + (uses_phi ? sizeof(cplx<R>) : 0);
+  const double blk_bytes = site * L * L * S::PPC;
+  return probed(PK_XY, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
+    XYArgs<R> b = a;
+    b.blk_count = cnt;
+    b.probe_inc = (unsigned long long)blk_bytes;
+    xy_pass<R, L, MODE><<<grid, S::THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  });
+}
+
+template <typename R, int L>
+cudaError_t launch_xy_L(int mode, const XYArgs<R>& a, cudaStream_t st) {
+  switch (mode) {
+    case XY_FWD: return launch_xy_t<R, L, XY_FWD>(a, st);
+    case XY_FWD_YINTDAG: return launch_xy_t<R, L, XY_FWD_YINTDAG>(a, st);
+    case XY_INV: return launch_xy_t<R, L, XY_INV>(a, st);
+    case XY_INV_Y: return launch_xy_t<R, L, XY_INV_Y>(a, st);
+    case XY_INV_YDAG: return launch_xy_t<R, L, XY_INV_YDAG>(a, st);
+    case XY_INV_Y_FWD: return launch_xy_t<R, L, XY_INV_Y_FWD>(a, st);
+    case XY_INV_PC: return launch_xy_t<R, L, XY_INV_PC>(a, st);
+    case XY_INV_PC_FWD: return launch_xy_t<R, L, XY_INV_PC_FWD>(a, st);
+    case XY_INV_ADD: return launch_xy_t<R, L, XY_INV_ADD>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, int NZ, int NT, int MUL>
+static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
+  using S = ZTShape<R, NZ, NT>;
+  constexpr int C = S::C;
+  const size_t smem = sizeof(cplx<R>) * NZ * NT * C * 4;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = set_smem(zt_pass<R, NZ, NT, MUL>, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  const long grid = (long)nrhs * a.ntiles;
+  if (grid == 0) return cudaSuccess;
+  // one block reads and writes C columns x NZ x NT sites of 4 spins and reads
+  // the momentum tables it needs (1 for Dslash, 2 for M0^-1)
+  const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));  // ZT_SCALAR: 2 tables too
+  return probed(PK_ZT, (int)sizeof(R), bytes, st, [&](unsigned long long* cnt) {
+    ZTArgs<R> b = a;
+    b.blk_count = cnt;
+    b.probe_inc = (unsigned long long)bytes;
+    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  });
+}
+
+template <typename R, int NZ, int NT>
+cudaError_t launch_zt_p(int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
+  switch (mul) {
+    case ZT_DSLASH: return launch_zt_t<R, NZ, NT, ZT_DSLASH>(a, nrhs, st);
+    case ZT_M0INV: return launch_zt_t<R, NZ, NT, ZT_M0INV>(a, nrhs, st);
+    case ZT_M0INV_DAG: return launch_zt_t<R, NZ, NT, ZT_M0INV_DAG>(a, nrhs, st);
+    case ZT_SCALAR:
+      if constexpr (sizeof(R) == 8) return launch_zt_t<R, NZ, NT, ZT_SCALAR>(a, nrhs, st);
+      break;
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, typename LO, int L, int MODE, bool PC>
+static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
+  using S = XYShape<L>;
+  const size_t smem = sizeof(cplx<R>) * S::PLANE * S::PPC + 33 * sizeof(double);
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaError_t e = set_smem(xy_cg<R, LO, L, MODE, PC>, smem);
+    if (e != cudaSuccess) return e;
+    attr_done = true;
+  }
+  dim3 grid(a.nblk, nrhs);
+  // algorithmic bytes of one block (PPC planes of L x L sites, 4 spins)
+  const double f = 4.0 * sizeof(cplx<R>), lo = 4.0 * sizeof(cplx<LO>), ph = sizeof(cplx<R>);
+  double site = 0.0;
+  int kind = PK_CG_P1;
+  switch (MODE) {
+    case CG_P1: site = 6 * f; kind = PK_CG_P1; break;                 // r, p, x in; p, A, x out
+    case CG_P3: site = 4 * f + ph; kind = PK_CG_P3; break;            // A, p in; C, A out; phi
+    case CG_P5: site = (a.shift != 0.0 ? 5 : 4) * f + (PC ? 0 : ph); kind = PK_CG_P5; break;  // A, C, r (p) in; r out
+    case RU_P1: site = 3 * f + 3 * lo; kind = PK_RU_P1; break;        // x_hi, x_lo, p in; x_hi, x_lo, A out
+    case RU_P5: site = 4 * f + lo + (PC ? 0 : ph); kind = PK_RU_P5; break;  // A, x_hi, C, b in; r out
+  }
+  const double blk_bytes = site * L * L * S::PPC;
+  return probed(kind, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
+    CGArgs<R, LO> b = a;
+    b.blk_count = cnt;
+    b.probe_inc = (unsigned long long)blk_bytes;
+    xy_cg<R, LO, L, MODE, PC><<<grid, S::THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  });
+}
+
+template <typename R, typename LO, int L, bool PC>
+static cudaError_t launch_cg_m(int mode, const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
+  switch (mode) {
+    case CG_P1: return launch_cg_t<R, LO, L, CG_P1, PC>(a, nrhs, st);
+    case CG_P3: return launch_cg_t<R, LO, L, CG_P3, PC>(a, nrhs, st);
+    case CG_P5: return launch_cg_t<R, LO, L, CG_P5, PC>(a, nrhs, st);
+    case RU_P1: return launch_cg_t<R, LO, L, RU_P1, PC>(a, nrhs, st);
+    case RU_P5: return launch_cg_t<R, LO, L, RU_P5, PC>(a, nrhs, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+template <typename R, typename LO, int L>
+cudaError_t launch_cg_L(bool pc, int mode, const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
+  return pc ? launch_cg_m<R, LO, L, true>(mode, a, nrhs, st) : launch_cg_m<R, LO, L, false>(mode, a, nrhs, st);
+}
+
+template <int L>
+cudaError_t launch_fk_L(int which, const ForceArgs<double>& a, dim3 grid, cudaStream_t st) {
+  using S = XYShape<L>;
+  const size_t smem = sizeof(cplx<double>) * S::PLANE * S::PPC + 33 * sizeof(double);
+  static bool done[3] = {false, false, false};
+  cudaError_t e = cudaSuccess;
+  if (!done[which]) {
+    if (which == FK_FORCE) e = set_smem(xy_force<L>, smem);
+    if (which == FK_BOSON_FWD) e = set_smem(xy_boson_fwd<L>, smem);
+    if (which == FK_BOSON_INV) e = set_smem(xy_boson_inv<L>, smem);
+    if (e != cudaSuccess) return e;
+    done[which] = true;
+  }
+  count_launch();
+  if (which == FK_FORCE) xy_force<L><<<grid, S::THREADS, smem, st>>>(a);
+  if (which == FK_BOSON_FWD) xy_boson_fwd<L><<<grid, S::THREADS, smem, st>>>(a);
+  if (which == FK_BOSON_INV) xy_boson_inv<L><<<grid, S::THREADS, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace wz

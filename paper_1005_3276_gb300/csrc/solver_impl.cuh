@@ -15,74 +15,6 @@
 
 namespace wz {
 
-template <typename R, typename LO, int L, int MODE, bool PC>
-static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
-  using S = XYShape<L>;
-  const size_t smem = sizeof(cplx<R>) * S::PLANE * S::PPC + 33 * sizeof(double);
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = set_smem(xy_cg<R, LO, L, MODE, PC>, smem);
-    if (e != cudaSuccess) return e;
-    attr_done = true;
-  }
-  dim3 grid(a.nblk, nrhs);
-  // algorithmic bytes of one block (PPC planes of L x L sites, 4 spins)
-  const double f = 4.0 * sizeof(cplx<R>), lo = 4.0 * sizeof(cplx<LO>), ph = sizeof(cplx<R>);
-  double site = 0.0;
-  int kind = PK_CG_P1;
-  switch (MODE) {
-    case CG_P1: site = 6 * f; kind = PK_CG_P1; break;                 // r, p, x in; p, A, x out
-    case CG_P3: site = 4 * f + ph; kind = PK_CG_P3; break;            // A, p in; C, A out; phi
-    case CG_P5: site = (a.shift != 0.0 ? 5 : 4) * f + (PC ? 0 : ph); kind = PK_CG_P5; break;  // A, C, r (p) in; r out
-    case RU_P1: site = 3 * f + 3 * lo; kind = PK_RU_P1; break;        // x_hi, x_lo, p in; x_hi, x_lo, A out
-    case RU_P5: site = 4 * f + lo + (PC ? 0 : ph); kind = PK_RU_P5; break;  // A, x_hi, C, b in; r out
-  }
-  const double blk_bytes = site * L * L * S::PPC;
-  return probed(kind, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
-    CGArgs<R, LO> b = a;
-    b.blk_count = cnt;
-    b.probe_inc = (unsigned long long)blk_bytes;
-    xy_cg<R, LO, L, MODE, PC><<<grid, S::THREADS, smem, st>>>(b);
-    return cudaGetLastError();
-  });
-}
-
-template <typename R, typename LO, int L, bool PC>
-static cudaError_t launch_cg_m(int mode, const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
-  switch (mode) {
-    case CG_P1: return launch_cg_t<R, LO, L, CG_P1, PC>(a, nrhs, st);
-    case CG_P3: return launch_cg_t<R, LO, L, CG_P3, PC>(a, nrhs, st);
-    case CG_P5: return launch_cg_t<R, LO, L, CG_P5, PC>(a, nrhs, st);
-    case RU_P1: return launch_cg_t<R, LO, L, RU_P1, PC>(a, nrhs, st);
-    case RU_P5: return launch_cg_t<R, LO, L, RU_P5, PC>(a, nrhs, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <typename R, typename LO>
-static cudaError_t launch_cg(int L, bool pc, int mode, const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
-  switch (L) {
-#define WZ_CASE(n)                                                           \
-  case n:                                                                    \
-    return pc ? launch_cg_m<R, LO, n, true>(mode, a, nrhs, st)               \
-              : launch_cg_m<R, LO, n, false>(mode, a, nrhs, st);
-    WZ_FOR_EXTENTS(WZ_CASE)
-#undef WZ_CASE
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <int L> static int nblk_of(int TZ) { return (TZ + XYShape<L>::PPC - 1) / XYShape<L>::PPC; }
-static int xy_nblk(int L, int TZ) {
-  switch (L) {
-#define WZ_CASE(n) \
-  case n: return nblk_of<n>(TZ);
-    WZ_FOR_EXTENTS(WZ_CASE)
-#undef WZ_CASE
-  }
-  return 0;
-}
-
 // Workspace layout (bytes) for a solve with iteration type RI.
 template <typename RI> struct SolverWS {
   size_t field_ri, field64, off_xlo, off_r, off_p, off_A, off_C, off_A64, off_C64, off_bt, off_xt, off_part,

@@ -216,7 +216,7 @@ __device__ __forceinline__ Philox4 member_draw(unsigned long long seed, int id, 
 
 // pi(x): Re, Im ~ N(0, 1); counter (site, 0, STREAM_MOMENTUM, traj); fields [member][V]
 // traj: device word holding the trajectory number (the counter word c3)
-__global__ void draw_momenta(cplx<double>* pi, long V, int nm, const int* mid, unsigned long long seed,
+static __global__ void draw_momenta(cplx<double>* pi, long V, int nm, const int* mid, unsigned long long seed,
                              const unsigned long long* trajp) {
   const unsigned traj = (unsigned)*trajp;
   const long n = (long)nm * V;
@@ -226,7 +226,7 @@ __global__ void draw_momenta(cplx<double>* pi, long V, int nm, const int* mid, u
 
 // R_k(x, s): density exp(-|R|^2); counter (site, 4k + s, STREAM_PSEUDOFERMION, traj),
 // k the pseudofermion within its member; fields [member][npf][V][4]
-__global__ void draw_sources(cplx<double>* R, int npf, long V, int nm, const int* mid, unsigned long long seed,
+static __global__ void draw_sources(cplx<double>* R, int npf, long V, int nm, const int* mid, unsigned long long seed,
                              const unsigned long long* trajp) {
   const unsigned traj = (unsigned)*trajp;
   const long n = (long)nm * npf * V * 4;
@@ -243,7 +243,7 @@ __global__ void draw_sources(cplx<double>* R, int npf, long V, int nm, const int
 }
 
 // partials of sum Re[conj(a) b] over n complex values per member, grid (nblk, members)
-__global__ void dot_re_partials(const cplx<double>* a, const cplx<double>* b, long n, double* part) {
+static __global__ void dot_re_partials(const cplx<double>* a, const cplx<double>* b, long n, double* part) {
   __shared__ double red[33];
   const long off = (long)blockIdx.y * n;
   double t = 0.0;
@@ -254,7 +254,7 @@ __global__ void dot_re_partials(const cplx<double>* a, const cplx<double>* b, lo
 }
 
 // phi += eps * pi (FP64 and its FP32 copy)
-__global__ void update_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* pi, double eps, long V) {
+static __global__ void update_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* pi, double eps, long V) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
     const cplx<double> f = phi[i] + eps * pi[i];
     phi[i] = f;
@@ -263,7 +263,7 @@ __global__ void update_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<dou
 }
 
 // pi -= eps * G
-__global__ void update_pi(cplx<double>* pi, const cplx<double>* G, double eps, long V) {
+static __global__ void update_pi(cplx<double>* pi, const cplx<double>* G, double eps, long V) {
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x)
     pi[i] = pi[i] - eps * G[i];
 }
@@ -285,7 +285,7 @@ __device__ __forceinline__ double serial_sum(const double* p, int n) {
   return t;
 }
 
-__global__ void metropolis(HParts h, double* out, int nm, const int* mid, unsigned long long seed,
+static __global__ void metropolis(HParts h, double* out, int nm, const int* mid, unsigned long long seed,
                            const unsigned long long* trajp) {
   const unsigned traj = (unsigned)*trajp;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -307,7 +307,7 @@ __global__ void metropolis(HParts h, double* out, int nm, const int* mid, unsign
 }
 
 // on rejection of member j: phi_j = phi0_j (FP64 and FP32 copies); fields [member][V]
-__global__ void restore_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* phi0, const double* res,
+static __global__ void restore_phi(cplx<double>* phi, cplx<float>* phi32, const cplx<double>* phi0, const double* res,
                             long V, int nm) {
   const long n = (long)nm * V;
   for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_symbol(wz):
 
 
 def test_supported_extents(wz):
-    for n in (4, 6, 8, 12, 16):
+    for n in (4, 6, 8, 12, 16, 32):
         assert wz.wz_supported_extent(n)
     for n in (5, 7, 0, -4, 1000):
         assert not wz.wz_supported_extent(n)

@@ -109,6 +109,24 @@ def test_empty_batch_is_noop(wz):
     lat.apply("M", x, x, 0)
 
 
+@pytest.mark.parametrize("dims", [(32, 32, 32, 32), (32, 16, 16, 16)])
+@pytest.mark.parametrize("dt", ["c128", "c64"])
+def test_apply_L32(wz, dims, dt):
+    """32-point lines (the 32^4 workload and the L = 32 apply sweep)."""
+    P = oracle.Params(dims=dims, m=0.02, g=1.0)
+    phi = synth.scalar_field(dims, 1.0, 0)
+    psi = synth.spinor_rhs(1, dims, 1)
+    lat = wz.Lattice(dims, m=P.m, g=P.g)
+    lat.set_phi(torch.from_numpy(phi).cuda())
+    tdt = torch.complex128 if dt == "c128" else torch.complex64
+    x = torch.from_numpy(psi).to(tdt).cuda()
+    y = torch.empty_like(x)
+    lat.apply("MdagM", x, y, 1)
+    torch.cuda.synchronize()
+    ref = oracle_apply("MdagM", P, phi, x.cpu().numpy().astype(np.complex128))
+    assert rel(y.cpu().numpy().astype(np.complex128), ref) < (TOL64 if dt == "c128" else TOL32)
+
+
 def test_full_size_sampled(wz):
     """16^4 with 12 right-hand sides (the precision workload), FP32 and FP64:
     two sampled right-hand sides checked in full against the oracle."""

@@ -99,7 +99,7 @@ def test_not_converged_and_zero_rhs(wz, small):
     assert rc == wz.WZ_OK and np.all(x == 0) and st["converged"] == w.nrhs
 
 
-@pytest.mark.parametrize("dims", [(12, 12, 12, 12), (32, 8, 8, 8)])
+@pytest.mark.parametrize("dims", [(12, 12, 12, 12), (32, 8, 8, 8), (32, 32, 32, 32)])
 def test_solve_other_shapes(wz, dims):
     P = oracle.Params(dims=dims, m=0.1, g=0.3)
     phi = synth.scalar_field(dims, 0.5, 7)

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory timing")
     ap.add_argument("--hmc-traj", type=int, default=2, help="timed trajectories per precision")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the L = 8, 16, 32 apply sweep")
+    ap.add_argument("--batch", action="store_true", help="also time the 64-lattice batched workload")
     return ap.parse_args()
 
 
@@ -307,6 +309,71 @@ def main():
         hmc["mixed_speedup"] = hmc["fp64"]["ms_per_traj"] / hmc["mixed"]["ms_per_traj"]
         hlat.close()
 
+    # apply-throughput sweep: (M^dag M) on L^4, FP32 vs FP64 fields, about 1M
+    # site-RHS per launch sequence (256 / 16 / 1 right-hand sides at L = 8/16/32)
+    sweep = None
+    if not args.no_sweep:
+        sweep = []
+        for L in (8, 16, 32):
+            dims = (L, L, L, L)
+            nr = max(1, (1 << 20) // (L ** 4))
+            slat = wz.Lattice(dims, m=w.m, g=w.g, stream=stream.cuda_stream)
+            slat.set_phi(torch.from_numpy(synth.scalar_field(dims, w.sigma, 0)).cuda())
+            row = {"L": L, "nrhs": nr}
+            for name, dt, S in (("fp32", torch.complex64, 32), ("fp64", torch.complex128, 64)):
+                x = torch.from_numpy(synth.spinor_rhs(nr, dims, 1)).to(dt).cuda()
+                y = torch.empty_like(x)
+                for _ in range(3):
+                    slat.apply("MdagM", x, y, nr)
+                reps = 10
+                flush.zero_()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    slat.apply("MdagM", x, y, nr)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms = e0.elapsed_time(e1) / reps
+                # five passes: 13 spinor fields + 2 phi per site-RHS
+                gbs = (13 * S + 2 * S // 4) * L ** 4 * nr / (ms / 1000.0) / 1e9
+                row[name] = {"applies_per_s": nr / (ms / 1000.0), "ms": ms, "GB_s": gbs}
+            row["fp32_over_fp64"] = row["fp32"]["applies_per_s"] / row["fp64"]["applies_per_s"]
+            sweep.append(row)
+            slat.close()
+
+    # batched workload: 64 lattices (16 each of 4^4, 8^4, 12^4, 16^4), (m, g)
+    # on an 8 x 8 grid, 8 right-hand sides each, one mixed solve to 1e-10
+    batch = None
+    if args.batch:
+        ws = synth.batch_workloads()
+        bt = wz.Batch([dict(dims=x.dims, m=x.m, g=x.g) for x in ws])
+        bs, xs = [], []
+        for i, x in enumerate(ws):
+            bt.set_phi(i, torch.from_numpy(synth.scalar_field(x.dims, x.sigma, 100 + i)).cuda())
+            bs.append(torch.from_numpy(synth.spinor_rhs(x.nrhs, x.dims, 200 + i)).cuda())
+            xs.append(torch.zeros_like(bs[-1]))
+        bt.solve(bs, xs, ws[0].nrhs, tol=1e-10)  # warm-up (graph capture)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        bst = bt.solve(bs, xs, ws[0].nrhs, tol=1e-10)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        applies = bst["total_iterations"] + bst["reliable_updates"]
+        site_rhs = sum(int(np.prod(x.dims)) * x.nrhs for x in ws)
+        batch = {"workload": "64 lattices: 16 each of 4^4, 8^4, 12^4, 16^4; m in linspace(0.02, 0.2, 8), "
+                             "g in linspace(0.1, 1.0, 8); 8 RHS each; mixed CG to 1e-10",
+                 "groups": bt.groups, "seconds": dt, "applies": applies, "applies_per_s": applies / dt,
+                 "site_rhs_applies_per_s": None, "max_iterations": bst["iterations"],
+                 "max_true_residual": bst["max_true_residual"], "site_rhs": site_rhs}
+        t0 = time.perf_counter()
+        tst = bt.trajectory(tau=0.1, nsteps=2, npf=8, tol=1e-10, seed=7, traj_index=0)
+        torch.cuda.synchronize()
+        batch["short_trajectory"] = {"tau": 0.1, "nsteps": 2, "npf": 8, "seconds": time.perf_counter() - t0,
+                                     "accepted": int(sum(x["accept"] for x in tst)),
+                                     "cg_iterations": int(tst[0]["cg_iterations"])}
+        bt.close()
+
     # end to end through the C ABI with pinned host buffers
     hb = torch.from_numpy(b).pin_memory()
     hx = torch.zeros_like(hb).pin_memory()
@@ -352,7 +419,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "apply_sweep": sweep, "batch": batch, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
         }))
     lat.close()

@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wz", choices=["wz", "reference"])
-    ap.add_argument("--probe", default="cg_p5", help="kernel class for the roofline probe (the dominant kernel)")
+    ap.add_argument("--probe", default="auto", help="kernel class for the roofline (auto: the dominant one)")
     ap.add_argument("--probe-bytes", type=int, default=4)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -251,11 +251,16 @@ def main():
     # kernel class on the launching stream; the probe makes the solver launch
     # its kernels one by one instead of replaying its graph, the kernels are
     # the same).
-    flush.zero_()
-    torch.cuda.synchronize()
-    wz.wz_probe_begin(args.probe, args.probe_bytes)
-    solve()
-    probe = wz.wz_probe_end()
+    probes = {}
+    for kind in ("zt", "cg_p1", "cg_p3", "cg_p5"):
+        flush.zero_()
+        torch.cuda.synchronize()
+        wz.wz_probe_begin(kind, args.probe_bytes)
+        solve()
+        probes[kind] = wz.wz_probe_end()
+    # the dominant kernel class: largest summed launch time over one solve
+    dom = args.probe if args.probe != "auto" else max(probes, key=lambda k: probes[k]["total_ms"])
+    probe = probes[dom]
 
     # max time over ranks, sum of work over ranks
     t_max, applies_all = total_ms, total_applies
@@ -397,7 +402,11 @@ def main():
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     achieved = probe["bytes"] / (probe["total_ms"] / 1000.0) / 1e9 if probe["total_ms"] > 0 else None
-    roofline = {"bound": "hbm", "kernel": f"{args.probe} (FP{8 * args.probe_bytes})",
+    kernels = {k: {"launches": v["launches"], "total_ms_per_solve": v["total_ms"],
+                   "avg_launch_us": 1000.0 * v["total_ms"] / max(1, v["timed_launches"]),
+                   "achieved_GB_s": v["bytes"] / (v["total_ms"] / 1000.0) / 1e9 if v["total_ms"] > 0 else None}
+               for k, v in probes.items()}
+    roofline = {"bound": "hbm", "kernel": f"{dom} (FP{8 * args.probe_bytes})",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_src,
                 "traffic": None, "launches": probe["launches"],
@@ -419,7 +428,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "apply_sweep": sweep, "batch": batch, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
         }))
     lat.close()

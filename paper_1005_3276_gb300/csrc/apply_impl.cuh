@@ -33,6 +33,9 @@ template <typename R> static XYArgs<R> xy_args(const wz_ctx* c, int nrhs) {
   a.rpm = rhs_per_member(c, nrhs);
   a.nplanes = nrhs * c->T * c->Z;
   a.TZ = c->T * c->Z;
+  a.Z = c->Z;
+  a.twc = tables<R>(c).twc;
+  a.tws = tables<R>(c).tws;
   return a;
 }
 

@@ -122,6 +122,9 @@ static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int 
     fa.phi = c->phi64;
     fa.kArr = c->k64;
     fa.rpm = npf;
+    fa.Z = c->Z;
+    fa.twc = c->t64.twc;
+    fa.tws = c->t64.tws;
     fa.TZ = TZ;
     fa.V = c->V;
     e = launch_fk(L, FK_FORCE, fa, dim3(w.nb, nr), s);

@@ -100,6 +100,9 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   ga.phi = phi_of<RI>(c);
   ga.kArr = karr_of<RI>(c);
   ga.rpm = rhs_per_member(c, nrhs);
+  ga.Z = c->Z;
+  ga.twc = tables<RI>(c).twc;
+  ga.tws = tables<RI>(c).tws;
   ga.shift = shift;
   ga.st = st;
   ga.nblk = nblk;
@@ -117,6 +120,9 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   ra.phi = c->phi64;
   ra.kArr = c->k64;
   ra.rpm = ga.rpm;
+  ra.Z = c->Z;
+  ra.twc = c->t64.twc;
+  ra.tws = c->t64.tws;
   ra.shift = shift;
   ra.st = st;
   ra.nblk = nblk;
@@ -178,6 +184,9 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     r3.phi = c->phi64;
     r3.kArr = c->k64;
     r3.rpm = ga.rpm;
+    r3.Z = c->Z;
+    r3.twc = c->t64.twc;
+    r3.tws = c->t64.tws;
     r3.shift = shift;
     r3.st = st;
     r3.nblk = nblk;

@@ -68,6 +68,9 @@ template <typename R, typename LO> struct CGArgs {
   const cplx<R>* phi;    // [member][T][Z][Y][X]
   const SiteCoef<R>* kArr;  // couplings per member
   int rpm;              // right-hand sides per member
+  int Z;                // planes per time slice (plane = t * Z + z)
+  const R* twc;         // cos / sin (pi t / T): antiperiodic twist (see xy_pass)
+  const R* tws;
   double shift;
   RhsState* st;
   double* part_out;     // [rhs][nblk] block partials written by this pass (may be null)
@@ -194,7 +197,13 @@ xy_cg(CGArgs<R, LO> a) {
     const int member = rhs / a.rpm;
     const long phib = ((long)member * a.TZ + plane_in) * (L * L) + x;
     const SiteCoef<R> kc = a.kArr[member];
-    if (INV) H::inv_y(P, w, s, v);
+    const int tt = plane_in / a.Z;
+    const cplx<R> twb{a.twc[tt], a.tws[tt]}, twf{a.twc[tt], -a.tws[tt]};
+    if (INV) {
+      H::inv_y(P, w, s, v);
+#pragma unroll
+      for (int y = 0; y < L; ++y) v[y] = twb * v[y];
+    }
 #pragma unroll
     for (int y = 0; y < L; ++y) {
       const long e = (site0 + y * L) * 4 + s;
@@ -239,7 +248,11 @@ xy_cg(CGArgs<R, LO> a) {
         v[y] = xv;
       }
     }
-    if (FWD) H::fwd_y(v, P, w, s);
+    if (FWD) {
+#pragma unroll
+      for (int y = 0; y < L; ++y) v[y] = twf * v[y];
+      H::fwd_y(v, P, w, s);
+    }
   }
   if constexpr (FWD) {
     __syncthreads();

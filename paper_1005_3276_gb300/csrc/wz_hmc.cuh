@@ -32,6 +32,9 @@ template <typename R> struct ForceArgs {
   const cplx<R>* phi;     // [member][V]
   const SiteCoef<R>* kArr;  // couplings per member
   int rpm;                // pseudofermions per member (xy_force)
+  int Z;                  // planes per time slice
+  const R* twc;           // antiperiodic twist cos / sin (pi t / T) (xy_force)
+  const R* tws;
   int TZ;
   int nblk;
   long V;
@@ -62,7 +65,13 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_force(ForceArgs<double
   cplx<R> v[L];
   if (live) H::inv_x(a.A + base, P, w, s, v);
   __syncthreads();
-  if (live) H::inv_y(P, w, s, v);
+  if (live) {
+    H::inv_y(P, w, s, v);
+    const int tt = plane_in / a.Z;
+    const cplx<R> twb{a.twc[tt], a.tws[tt]};
+#pragma unroll
+    for (int y = 0; y < L; ++y) v[y] = twb * v[y];
+  }
   const int member = k / a.rpm;
   const SiteCoef<R> kc = a.kArr[member];
   const cplx<R> cg{kc.cg_re, kc.cg_im};

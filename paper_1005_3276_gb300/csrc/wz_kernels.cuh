@@ -10,9 +10,10 @@
 //             its "phase B" owns y-lines in POSITION space, so every
 //             site-local term (mass, Yukawa, CG vector updates, force
 //             contractions) is fused there.
-//   zt pass : a tile of C consecutive (y, x) columns for all (z, t); forward
-//             FFT over (z, t) with the antiperiodic twist exp(-i pi t/T),
-//             momentum-space spin multiply, inverse FFT, untwist.  In place.
+//   zt pass : a tile of C consecutive (p_x, p_y) columns for all (z, t);
+//             forward FFT over (z, t), momentum-space spin multiply, inverse
+//             FFT.  In place.  The antiperiodic twist exp(-+i pi t/T) is a
+//             per-plane constant applied by the xy passes in position space.
 //
 // M = xy_fwd -> zt(+Dslash) -> xy_inv(+Y psi); M^dagger M fuses the middle xy
 // passes (inverse, + Y psi, store M psi, forward) so it takes five passes.
@@ -82,6 +83,9 @@ template <typename R> struct XYArgs {
   R shift;
   int nplanes;           // nrhs * T * Z
   int TZ;                // planes per right-hand side
+  int Z;                 // planes per time slice (plane = t * Z + z)
+  const R* twc;          // cos(pi t / T): antiperiodic twist, applied in position space
+  const R* tws;          // sin(pi t / T)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
@@ -175,10 +179,17 @@ xy_pass(XYArgs<R> a) {
     const int member = (int)(plane / a.TZ) / a.rpm;
     const long phib = ((long)member * a.TZ + plane % a.TZ) * (long)(L * L) + x;
     const SiteCoef<R> kc = a.kArr[member];
+    // antiperiodic time: the field is multiplied by exp(-i pi t/T) before the
+    // forward transform and by exp(+i pi t/T) after the inverse one, so that
+    // the plain DFT over t lands on p_t = pi (2n + 1)/T (Sec. 3.1)
+    const int tt = (int)((plane % a.TZ) / a.Z);
+    const cplx<R> twb{a.twc[tt], a.tws[tt]}, twf{a.twc[tt], -a.tws[tt]};
     if (I::inv) {
 #pragma unroll
       for (int y = 0; y < L; ++y) v[y] = P[y * S::RP + x * 4 + s];
       fft_line<L, +1, R>(v);
+#pragma unroll
+      for (int y = 0; y < L; ++y) v[y] = twb * v[y];
     }
 #pragma unroll
     for (int y = 0; y < L; ++y) {
@@ -206,6 +217,8 @@ xy_pass(XYArgs<R> a) {
       }
     }
     if (I::fwd) {
+#pragma unroll
+      for (int y = 0; y < L; ++y) v[y] = twf * v[y];
       fft_line<L, -1, R>(v);
     }
   }
@@ -298,10 +311,9 @@ zt_pass(ZTArgs<R> a) {
   // ---------------- z-phase (forward): thread owns (t = q, column, s)
   if (q < NT) {
     const int t = q;
-    // exp(-i pi t / T) for the antiperiodic fermion; 1 for the periodic scalar
-    const cplx<R> tw = MUL == ZT_SCALAR ? cplx<R>{R(1), R(0)} : cplx<R>{a.twc[t], -a.tws[t]};
+    // (the antiperiodic twist of the fermion is applied by the xy passes)
 #pragma unroll
-    for (int z = 0; z < NZ; ++z) v[z] = colok ? tw * A[((long)t * ZXY + (long)z * a.XY) * 4] : cplx<R>{R(0), R(0)};
+    for (int z = 0; z < NZ; ++z) v[z] = colok ? A[((long)t * ZXY + (long)z * a.XY) * 4] : cplx<R>{R(0), R(0)};
     fft_ptr<NZ, -1, R>(v);
 #pragma unroll
     for (int z = 0; z < NZ; ++z) sm[((t * NZ + z) * C + c) * 4 + s] = v[z];
@@ -364,13 +376,12 @@ zt_pass(ZTArgs<R> a) {
   // ---------------- z-phase (inverse) and untwist exp(+i pi t / T)
   if (q < NT) {
     const int t = q;
-    const cplx<R> tw = MUL == ZT_SCALAR ? cplx<R>{R(1), R(0)} : cplx<R>{a.twc[t], a.tws[t]};
 #pragma unroll
     for (int z = 0; z < NZ; ++z) v[z] = sm[((t * NZ + z) * C + c) * 4 + s];
     fft_ptr<NZ, +1, R>(v);
     if (colok) {
 #pragma unroll
-      for (int z = 0; z < NZ; ++z) A[((long)t * ZXY + (long)z * a.XY) * 4] = tw * v[z];
+      for (int z = 0; z < NZ; ++z) A[((long)t * ZXY + (long)z * a.XY) * 4] = v[z];
     }
   }
 }

@@ -5,8 +5,11 @@
 // device state, so a chunk is a fixed launch sequence and the host only reads
 // the per-RHS state between chunks to see whether all have finished.
 #pragma once
+#include <algorithm>
 #include <chrono>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "apply_impl.cuh"
@@ -151,6 +154,12 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   } while (0)
   const int max_chunks = maxiter / K + 64;
 
+  // Right-hand sides are iterated in groups of gsz: the five passes of one
+  // group run back to back, so its working set (five spinor fields per RHS)
+  // can stay in L2 between producer and consumer passes.  The group size is
+  // chosen per solve shape by timing the candidates (autotune_group below).
+  int gsz = nrhs;
+
   // one chunk: K iterations and one reliable-update block, all gated on the device
   auto issue_chunk = [&](cudaStream_t q) -> cudaError_t {
     cudaError_t e2;
@@ -160,17 +169,27 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     if (e2 != cudaSuccess) return e2;      \
   } while (0)
     for (int k = 0; k < K; ++k) {
-      CGArgs<RI, RI> a1 = ga;
-      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P1, a1, nrhs, q));
-      WZ_Q(launch_zt<RI>(c->Z, c->T, mul1, z1, nrhs, q));
-      CGArgs<RI, RI> a3 = ga;
-      a3.part_out = part3;
-      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P3, a3, nrhs, q));
-      WZ_Q(launch_zt<RI>(c->Z, c->T, mul2, z2, nrhs, q));
-      CGArgs<RI, RI> a5 = ga;
-      a5.part_in = part3;
-      a5.part_out = part5;
-      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, nrhs, q));
+      for (int r0 = 0; r0 < nrhs; r0 += gsz) {
+        const int ng = nrhs - r0 < gsz ? nrhs - r0 : gsz;
+        CGArgs<RI, RI> a1 = ga;
+        a1.rhs0 = r0;
+        WZ_Q(launch_cg<RI, RI>(L, pc, CG_P1, a1, ng, q));
+        ZTArgs<RI> zz1 = z1;
+        zz1.rhs0 = r0;
+        WZ_Q(launch_zt<RI>(c->Z, c->T, mul1, zz1, ng, q));
+        CGArgs<RI, RI> a3 = ga;
+        a3.rhs0 = r0;
+        a3.part_out = part3;
+        WZ_Q(launch_cg<RI, RI>(L, pc, CG_P3, a3, ng, q));
+        ZTArgs<RI> zz2 = z2;
+        zz2.rhs0 = r0;
+        WZ_Q(launch_zt<RI>(c->Z, c->T, mul2, zz2, ng, q));
+        CGArgs<RI, RI> a5 = ga;
+        a5.rhs0 = r0;
+        a5.part_in = part3;
+        a5.part_out = part5;
+        WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, ng, q));
+      }
       count_launch();
       cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter, c->counters);
       WZ_Q(cudaGetLastError());
@@ -203,6 +222,63 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
 #undef WZ_Q
     return cudaSuccess;
   };
+
+  // Autotune the RHS group size once per solve shape: for each candidate,
+  // re-initialise and time two chunks (16 iterations) with CUDA events.
+  {
+    static std::mutex mu;
+    static std::map<std::vector<long>, int> cache;
+    const std::vector<long> tkey{(long)sizeof(RI), (long)pc, (long)c->T, (long)c->Z, (long)c->X, (long)nrhs,
+                                 (long)c->nm};
+    int found = 0;
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      auto it = cache.find(tkey);
+      if (it != cache.end()) found = it->second;
+    }
+    if (found) {
+      gsz = found;
+    } else if (nrhs > 1 && !inline_capture && !g_probe.active) {
+      std::vector<int> cand;
+      for (int d : {1, 2, 3, 4, 6, 8})
+        if (nrhs / d >= 1) {
+          const int g = (nrhs + d - 1) / d;
+          if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+        }
+      cudaEvent_t e0, e1;
+      WZ_RUN(cudaEventCreate(&e0));
+      WZ_RUN(cudaEventCreate(&e1));
+      float best = 1e30f;
+      int bestg = nrhs;
+      for (int g : cand) {
+        gsz = g;
+        WZ_RUN(issue_chunk(s));  // warm-up on whatever state the recursion is in
+        WZ_RUN(cudaEventRecord(e0, s));
+        WZ_RUN(issue_chunk(s));
+        WZ_RUN(issue_chunk(s));
+        WZ_RUN(cudaEventRecord(e1, s));
+        WZ_RUN(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        WZ_RUN(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bestg = g;
+        }
+        // back to the initial state of the solve
+        WZ_RUN(cudaMemsetAsync(xs, 0, W.field64, s));
+        count_launch(2);
+        cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, p, n_per_rhs, partR, 64);
+        WZ_RUN(cudaGetLastError());
+        cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol);
+        WZ_RUN(cudaGetLastError());
+      }
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      gsz = bestg;
+      std::lock_guard<std::mutex> lk(mu);
+      cache[tkey] = gsz;
+    }
+  }
 
   // Graph mode: the whole chunk loop is one CUDA graph whose body sits in a
   // WHILE conditional node; a one-thread kernel at the end of the body keeps
@@ -266,6 +342,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     key.ws_bytes = c->ws_solver.bytes;
     key.phi64 = c->phi64;
     key.phi32 = c->phi32;
+    key.gsz = gsz;
     if (!G.exec || memcmp(&key, &G.key, sizeof(key)) != 0) {
       G.release();
       WZ_CUDA_TRY(c, cudaGraphCreate(&G.graph, 0));

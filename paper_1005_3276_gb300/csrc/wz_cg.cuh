@@ -78,6 +78,7 @@ template <typename R, typename LO> struct CGArgs {
   int nblk;             // blocks per right-hand side
   int TZ;               // planes per right-hand side
   int gate_ru;          // 1: act on RHS with a pending reliable update; 0: on running RHS
+  int rhs0;             // first right-hand side of this launch (blockIdx.y counts from it)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
@@ -128,7 +129,7 @@ xy_cg(CGArgs<R, LO> a) {
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
   double* red = reinterpret_cast<double*>(sm + S::PLANE * S::PPC);  // 33 doubles
 
-  const int rhs = blockIdx.y;
+  const int rhs = blockIdx.y + a.rhs0;
   RhsState* st = a.st + rhs;
   if (!(a.gate_ru ? st->ru : st->run)) return;  // whole block, before any barrier
 

@@ -61,6 +61,7 @@ struct SolverGraphKey {
   size_t ws_bytes;
   const void* phi64;
   const void* phi32;
+  int gsz;  // right-hand sides per group
 };
 struct SolverGraph {
   SolverGraphKey key{};

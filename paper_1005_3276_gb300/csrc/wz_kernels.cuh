@@ -262,6 +262,7 @@ template <typename R> struct ZTArgs {
   int X, XY;
   const int* gate;     // optional per-RHS run flag: block returns if gate[rhs * gate_stride] == 0
   int gate_stride;
+  int rhs0;            // first right-hand side of this launch (launches may cover a group of RHS)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
@@ -284,7 +285,7 @@ template <typename R, int NZ, int NT> struct ZTShape {
 };
 
 template <typename R, int NZ, int NT, int MUL>
-__global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS)
+__global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS, (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256) ? 4 : 1)
 zt_pass(ZTArgs<R> a) {
   constexpr int C = ZTShape<R, NZ, NT>::C;
   extern __shared__ unsigned char smem_raw[];
@@ -294,7 +295,7 @@ zt_pass(ZTArgs<R> a) {
   const int s = tid & 3;
   const int c = (tid >> 2) % C;
   const int q = tid / (4 * C);  // t in the z-phase, z in the t-phase
-  const int rhs = blockIdx.x / a.ntiles;
+  const int rhs = blockIdx.x / a.ntiles + a.rhs0;
   if (a.gate && !a.gate[(long)rhs * a.gate_stride]) return;  // whole block, before any barrier
   if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
   const int col_raw = (blockIdx.x % a.ntiles) * C + c;  // (p_x, p_y) column = p_x * Y + p_y

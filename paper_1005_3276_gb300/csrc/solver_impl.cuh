@@ -7,6 +7,7 @@
 #pragma once
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -236,7 +237,10 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       auto it = cache.find(tkey);
       if (it != cache.end()) found = it->second;
     }
-    if (found) {
+    const char* forced = getenv("WZ_RHS_GROUP");  // a fixed group size overrides the tuner
+    if (forced && atoi(forced) > 0) {
+      gsz = atoi(forced) < nrhs ? atoi(forced) : nrhs;
+    } else if (found) {
       gsz = found;
     } else if (nrhs > 1 && !inline_capture && !g_probe.active) {
       std::vector<int> cand;

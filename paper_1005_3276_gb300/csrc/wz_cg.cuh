@@ -34,6 +34,12 @@
 #pragma once
 #include "wz_kernels.cuh"
 
+// blocks per SM the CG passes are compiled for (85 registers a thread at 256
+// threads); measured against 1, 2 and 4 on the 16^4 x 12 RHS solve
+#ifndef WZ_XY_MINB
+#define WZ_XY_MINB 3
+#endif
+
 namespace wz {
 
 struct RhsState {
@@ -119,7 +125,7 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 }
 
 template <typename R, typename LO, int L, int MODE, bool PC>
-__global__ void __launch_bounds__(XYShape<L>::THREADS)
+__global__ void __launch_bounds__(XYShape<L>::THREADS, WZ_XY_MINB)
 xy_cg(CGArgs<R, LO> a) {
   using S = XYShape<L>;
   using H = XYPhase<R, L>;

@@ -190,6 +190,20 @@ int wz_md_integrate(wz_ctx* ctx, void* pi, const void* eta, int npf, const wz_hm
  * device with a Philox uniform; on rejection phi is restored.  Synchronous. */
 int wz_trajectory(wz_ctx* ctx, const wz_hmc_params* h, wz_traj_stats* st);
 
+/* ---- observables ----
+ *
+ * Auxiliary-field VEV (Sec. 7.5): F~ = -(1 - D2/2)(m^* phi^* + g^* phi^*2) on the
+ * equation of motion of Eq. lata; since (1 - D2/2)(p = 0) = 1 its volume average
+ * is -(1/V) sum_x (m^* phi^* + g^* phi^*2).  F receives (re, im) per member of
+ * the context (2 doubles for a single lattice).  Synchronous. */
+int wz_aux_vev(wz_ctx* ctx, double* F);
+
+/* Locality probe of Dslash (Sec. 3.2, Eq. uir): psi = Dslash eta for a unit
+ * point source eta (spin 0 at the origin); f[r] = max ||psi(x)|| over the sites
+ * at taxi-driver distance r = sum_mu min(|x_mu|, L_mu - |x_mu|).  f needs
+ * T/2 + Z/2 + Y/2 + X/2 + 1 entries (nf); FP64.  Synchronous. */
+int wz_locality(wz_ctx* ctx, double* f, int nf);
+
 /* ---- batches of independent lattices (replicas of uneven extent and coupling) ----
  *
  * A batch holds n lattices, each with its own dims, m, g and phi (e.g. the

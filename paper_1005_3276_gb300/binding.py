@@ -106,6 +106,8 @@ def _load():
         "wz_batch_solve": ([P, ctypes.POINTER(P), ctypes.POINTER(P), I, D, I, ctypes.c_uint,
                             ctypes.POINTER(WzSolveStats)], I),
         "wz_batch_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
+        "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
+        "wz_locality": ([P, ctypes.POINTER(D), I], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
         "wz_probe_begin": ([I, I], I),
         "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
@@ -123,7 +125,7 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_solve", "wz_apply_mdagm_noalloc", "wz_get_phi", "wz_force", "wz_md_integrate",
            "wz_trajectory", "wz_batch_create", "wz_batch_destroy", "wz_batch_last_error", "wz_batch_size",
            "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
-           "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
+           "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
 def _is_torch(x):
@@ -255,6 +257,21 @@ def wz_trajectory(ctx, params):
     return st.as_dict()
 
 
+def wz_aux_vev(ctx, nm=1):
+    """(1/V) sum_x F~(x) per member, as a list of complex numbers."""
+    out = (ctypes.c_double * (2 * nm))()
+    check(ctx, LIB.wz_aux_vev(ctx, out))
+    return [complex(out[2 * j], out[2 * j + 1]) for j in range(nm)]
+
+
+def wz_locality(ctx, dims):
+    """f(r), r = 0 .. T/2 + Z/2 + Y/2 + X/2, of Dslash on a point source."""
+    n = sum(int(d) // 2 for d in dims) + 1
+    out = (ctypes.c_double * n)()
+    check(ctx, LIB.wz_locality(ctx, out, n))
+    return np.array(list(out))
+
+
 def wz_kernel_launches():
     return int(LIB.wz_kernel_launches())
 
@@ -310,6 +327,12 @@ class Lattice:
 
     def get_phi(self, phi):
         return wz_get_phi(self.ctx, phi)
+
+    def aux_vev(self):
+        return wz_aux_vev(self.ctx)[0]
+
+    def locality(self):
+        return wz_locality(self.ctx, self.dims)
 
     def force(self, eta, grad, tol=1e-10, parts=WZ_FORCE_FERMION | WZ_FORCE_BOSON):
         npf = 0 if eta is None else self._nrhs(eta)

@@ -22,7 +22,11 @@ Ginsparg-Wilson fermions"):
                    with and without the M0^-1 preconditioning (Eq. theprob).
 * ``force``        bosonic action of Eq. acws and its gradient; pseudofermion
                    action eta^dagger (M^dagger M)^-1 eta and its gradient.
-* ``hmc``          leapfrog / Omelyan molecular dynamics and the Metropolis step.
+* ``rational``     minimax relative rational approximations of x^gamma (Remez
+                   exchange in mpmath) and r(M^dagger M) eta by shifted solves
+                   (Eqs. jkjk, hbeq, yuier); Zolotarev's x^-1/2 as a pin.
+* ``hmc``          leapfrog / Omelyan molecular dynamics and the Metropolis step;
+                   RHMC with rational action and heatbath.
 * ``philox``       Philox4x32-10 counter-based generator (Salmon et al., SC'11)
                    and Box-Muller Gaussians, so that random draws made on the
                    device can be reproduced here bit for bit.

@@ -11,6 +11,11 @@ Pseudofermion action with one pole (the single-pole form of Eq. jkjk, alpha=1):
 
     S_pf = eta^dagger (M^dagger M + beta)^-1 eta.
 
+With the rational approximation of Eq. jkjk, r(x) = alpha_0 + sum_i alpha_i/(x + beta_i)
+(``rational``), the pseudofermion action is eta^dagger r(M^dagger M) eta; alpha_0 eta^dagger eta
+does not depend on phi, so its force is the alpha_i-weighted sum of single-pole forces
+with shifts beta_i.
+
 Forces are returned as the complex array G = dS/dphi_R + i dS/dphi_I, i.e. the
 gradient with respect to the real and imaginary parts of phi at every site.
 
@@ -24,6 +29,7 @@ import numpy as np
 
 from . import cg as cg_mod
 from . import fftops
+from . import rational
 
 
 def superpotential_derivative(params, phi):
@@ -75,3 +81,16 @@ def auxiliary_vev(params, phi):
     """
     w = np.conj(params.m) * np.conj(phi) + np.conj(params.g) * np.conj(phi) ** 2
     return complex(-np.mean(fftops.apply_K_scalar(params, w)))
+
+
+def rational_pf_action(params, phi, eta, coef, tol=1e-13):
+    """eta^dagger r(M^dagger M) eta with r of Eq. jkjk (coefficients ``coef``)."""
+    return float(np.vdot(eta, rational.rational_apply(params, phi, eta, coef, tol)).real)
+
+
+def rational_pf_force(params, phi, eta, coef, tol=1e-13):
+    """Gradient of ``rational_pf_action``: sum_i alpha_i G_pf(beta_i)."""
+    G = np.zeros(phi.shape, dtype=complex)
+    for a, b in zip(coef["alpha"], coef["beta"]):
+        G = G + a * pf_force(params, phi, eta, float(b), tol)
+    return G

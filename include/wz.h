@@ -104,8 +104,9 @@ int wz_apply(wz_ctx* ctx, int op, int dtype, const void* in, void* out, int nrhs
 enum wz_solve_flags {
   WZ_SOLVE_MIXED = 1,     /* FP32 iteration with FP64 reliable updates (Sec. 7.4 suggests
                              mixed precision after Clark et al.); else FP64 throughout */
-  WZ_SOLVE_PC = 2         /* M0^-1 preconditioning of Sec. 7.3 (Eq. theprob); shift must be 0
-                             (a shifted system needs beta M0^-1dag M0^-1, Eq. yuier, not built) */
+  WZ_SOLVE_PC = 2         /* M0^-1 preconditioning of Sec. 7.3 (Eq. theprob); a shifted system
+                             is solved as (M~^dag M~ + shift M0^-1dag M0^-1) x~ = b~, the
+                             form Sec. 7.4 gives for Eq. yuier */
 };
 
 typedef struct wz_solve_stats {
@@ -129,6 +130,57 @@ typedef struct wz_solve_stats {
  * nrhs FP64 true relative residuals of the original system. */
 int wz_solve(wz_ctx* ctx, const void* b, void* x, int nrhs, double shift, double tol, int maxiter,
              unsigned flags, wz_solve_stats* stats, double* resid);
+
+/* Shifted systems of a rational approximation (Eq. yuier): for every shift
+ * beta_i (i < nshift <= 64, beta_i >= 0) and right-hand side b_j (j < nrhs),
+ * solve (M^dagger M + beta_i) x_ij = b_j, all nshift * nrhs systems as
+ * right-hand sides of one batched CG (each stops on its own residual, as in
+ * wz_solve).  x holds nshift * nrhs complex128 fields ordered
+ * [member][shift][rhs of the member] (a single lattice: [shift][rhs]).
+ * Flags, tolerance, host/device pointers and return codes as wz_solve; stats
+ * cover all systems, resid (may be NULL) gets nshift * nrhs residuals in x's
+ * order. */
+int wz_solve_multishift(wz_ctx* ctx, const void* b, void* x, int nrhs, int nshift, const double* shifts,
+                        double tol, int maxiter, unsigned flags, wz_solve_stats* stats, double* resid);
+
+/* ---- rational approximations (Eqs. jkjk, hbeq; Sec. 7.4) ----
+ *
+ * x^power ~ r(x) = a0 + sum_{i<d} alpha_i / (x + beta_i) on [lo, hi]: the
+ * pseudofermion action uses power -1/4 (phase-quenched |Pf| = det(M^dag M)^1/4),
+ * the heatbath +1/8.  The paper asks for error-minimising coefficients and prints
+ * none; wz_rational_minimax computes the minimax RELATIVE error approximation of
+ * type (d, d) (Remez exchange; see remez.cu for the method). */
+#define WZ_RATIONAL_MAX 64
+typedef struct wz_rational {
+  int d;                          /* poles, 0 <= d <= WZ_RATIONAL_MAX */
+  double a0;                      /* alpha_0 */
+  double alpha[WZ_RATIONAL_MAX];  /* residues alpha_1 .. alpha_d (entries >= d unused) */
+  double beta[WZ_RATIONAL_MAX];   /* shifts beta_1 .. beta_d > 0, ascending */
+  double power;                   /* the exponent approximated (informational) */
+  double lo, hi;                  /* interval asked for */
+  double build_lo, build_hi;      /* interval the exchange ran on (wider where double
+                                     precision could not resolve the optimum on [lo, hi]) */
+  double err;                     /* max |r(x)/x^power - 1| over [lo, hi], measured */
+} wz_rational;
+
+/* Minimax relative approximation of x^power, 0 < |power| < 1, on 0 < lo < hi,
+ * degree d.  Host-only computation (no context, no GPU).  WZ_EINVAL on bad
+ * arguments, WZ_NOT_CONVERGED if the exchange failed. */
+int wz_rational_minimax(double power, double lo, double hi, int d, wz_rational* out);
+
+/* Spectral interval of the free operator M0^dagger M0 = D_mu^dag D_mu + |m|^2
+ * (Sec. 7.3) over the lattice momenta: the range Sec. 7.4 uses for the
+ * approximations at weak coupling.  lo, hi: host doubles.  Synchronous. */
+int wz_spectral_bounds(wz_ctx* ctx, double* lo, double* hi);
+
+/* out = r(M^dagger M) in = a0 in + sum_i alpha_i (M^dagger M + beta_i)^-1 in for
+ * nrhs complex128 fields (host or device; out must not alias in), with the d
+ * shifted solves of Eq. yuier batched in one CG to tolerance tol.  With
+ * WZ_SOLVE_PC in flags the poles beta_i <= pc_cutoff are solved with the M0^-1
+ * preconditioning (the paper uses it up to beta = 100, Sec. 7.4) and the rest
+ * without (single-lattice contexts).  Synchronous; stats cover every solve. */
+int wz_rational_apply(wz_ctx* ctx, const wz_rational* r, const void* in, void* out, int nrhs, double tol,
+                      int maxiter, unsigned flags, double pc_cutoff, wz_solve_stats* stats);
 
 /* ---- forces, actions, molecular dynamics, HMC (Eq. acws; Sec. 7.2) ----
  *
@@ -189,6 +241,21 @@ int wz_md_integrate(wz_ctx* ctx, void* pi, const void* eta, int npf, const wz_hm
  * H = |pi|^2/2 + S_B + S_pf in FP64, molecular dynamics, Metropolis on the
  * device with a Philox uniform; on rejection phi is restored.  Synchronous. */
 int wz_trajectory(wz_ctx* ctx, const wz_hmc_params* h, wz_traj_stats* st);
+
+/* RHMC (Secs. 7.2, 7.4): the pseudofermion action is S_pf = sum_k eta_k^dag
+ * r_a(M^dag M) eta_k with r_a ~ x^-1/4 (wz_rational), its force the
+ * alpha_i-weighted sum of single-pole forces at shifts beta_i.  As wz_force with
+ * the rational action (r_a->d shifted solves per pseudofermion, batched). */
+int wz_rhmc_force(wz_ctx* ctx, const void* eta, int npf, const wz_rational* action, double tol, unsigned parts,
+                  void* grad, double* S_B, double* S_pf, wz_solve_stats* stats);
+
+/* One RHMC trajectory: as wz_trajectory, with the heatbath eta_k = r_h(M^dag M) R_k
+ * (r_h ~ x^1/8, Eq. hbeq) and the rational action r_a for H and the force.
+ * S_pf at both ends is evaluated with r_a from the solves of the first and last
+ * force evaluations.  h->npf pseudofermions; h->tol for every solve.  In graph
+ * mode the whole trajectory (both solve kinds included) is one CUDA graph. */
+int wz_rhmc_trajectory(wz_ctx* ctx, const wz_hmc_params* h, const wz_rational* action, const wz_rational* heatbath,
+                       wz_traj_stats* st);
 
 /* ---- observables ----
  *

@@ -63,6 +63,38 @@ class WzTrajStats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+WZ_RATIONAL_MAX = 64
+
+
+class WzRational(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int), ("a0", ctypes.c_double), ("alpha", ctypes.c_double * WZ_RATIONAL_MAX),
+                ("beta", ctypes.c_double * WZ_RATIONAL_MAX), ("power", ctypes.c_double), ("lo", ctypes.c_double),
+                ("hi", ctypes.c_double), ("build_lo", ctypes.c_double), ("build_hi", ctypes.c_double),
+                ("err", ctypes.c_double)]
+
+    def as_dict(self):
+        d = int(self.d)
+        return {"d": d, "a0": self.a0, "alpha": np.array(self.alpha[:d]), "beta": np.array(self.beta[:d]),
+                "gamma": self.power, "lo": self.lo, "hi": self.hi, "build_lo": self.build_lo,
+                "build_hi": self.build_hi, "err": self.err}
+
+
+def rational_struct(coef):
+    """WzRational from a mapping with a0, alpha, beta (and optional gamma, lo, hi, err)."""
+    r = WzRational()
+    alpha, beta = list(coef["alpha"]), list(coef["beta"])
+    if len(alpha) != len(beta) or len(alpha) > WZ_RATIONAL_MAX:
+        raise ValueError("alpha and beta need the same length <= 64")
+    r.d = len(alpha)
+    r.a0 = float(coef["a0"])
+    for i, (a, b) in enumerate(zip(alpha, beta)):
+        r.alpha[i], r.beta[i] = float(a), float(b)
+    r.power = float(coef.get("gamma", 0.0))
+    r.lo, r.hi = float(coef.get("lo", 0.0)), float(coef.get("hi", 0.0))
+    r.err = float(coef.get("err", 0.0))
+    return r
+
+
 WZ_FORCE_FERMION, WZ_FORCE_BOSON = 1, 2
 WZ_HMC_FP64_SOLVES, WZ_HMC_NO_METROPOLIS = 1, 2
 INTEGRATORS = {"leapfrog": 0, "omelyan": 1}
@@ -106,6 +138,16 @@ def _load():
         "wz_batch_solve": ([P, ctypes.POINTER(P), ctypes.POINTER(P), I, D, I, ctypes.c_uint,
                             ctypes.POINTER(WzSolveStats)], I),
         "wz_batch_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
+        "wz_solve_multishift": ([P, P, P, I, I, ctypes.POINTER(D), D, I, ctypes.c_uint,
+                                 ctypes.POINTER(WzSolveStats), ctypes.POINTER(D)], I),
+        "wz_rational_minimax": ([D, D, D, I, ctypes.POINTER(WzRational)], I),
+        "wz_spectral_bounds": ([P, ctypes.POINTER(D), ctypes.POINTER(D)], I),
+        "wz_rational_apply": ([P, ctypes.POINTER(WzRational), P, P, I, D, I, ctypes.c_uint, D,
+                               ctypes.POINTER(WzSolveStats)], I),
+        "wz_rhmc_force": ([P, P, I, ctypes.POINTER(WzRational), D, ctypes.c_uint, P, ctypes.POINTER(D),
+                           ctypes.POINTER(D), ctypes.POINTER(WzSolveStats)], I),
+        "wz_rhmc_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzRational),
+                                ctypes.POINTER(WzRational), ctypes.POINTER(WzTrajStats)], I),
         "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
         "wz_locality": ([P, ctypes.POINTER(D), I], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
@@ -125,6 +167,8 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_solve", "wz_apply_mdagm_noalloc", "wz_get_phi", "wz_force", "wz_md_integrate",
            "wz_trajectory", "wz_batch_create", "wz_batch_destroy", "wz_batch_last_error", "wz_batch_size",
            "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
+           "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
+           "wz_rhmc_force", "wz_rhmc_trajectory",
            "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
@@ -257,6 +301,70 @@ def wz_trajectory(ctx, params):
     return st.as_dict()
 
 
+def wz_solve_multishift(ctx, b, x, nrhs, shifts, tol=1e-10, maxiter=100000, flags=WZ_SOLVE_MIXED, resid=False,
+                        raise_on_nonconvergence=True):
+    """x[i * nrhs + j] = (M^dag M + shifts[i])^-1 b[j]; returns (status, stats, residuals or None)."""
+    pb, _ = field_ptr(b, WZ_C128)
+    px, _ = field_ptr(x, WZ_C128)
+    sh = (ctypes.c_double * len(shifts))(*[float(v) for v in shifts])
+    st = WzSolveStats()
+    nsys = int(nrhs) * len(shifts)
+    res = (ctypes.c_double * max(nsys, 1))() if resid else None
+    rc = LIB.wz_solve_multishift(ctx, pb, px, int(nrhs), len(shifts), sh, float(tol), int(maxiter), int(flags),
+                                 ctypes.byref(st), res)
+    if rc not in (WZ_OK, WZ_NOT_CONVERGED) or (rc == WZ_NOT_CONVERGED and raise_on_nonconvergence):
+        check(ctx, rc)
+    return rc, st.as_dict(), (list(res)[:nsys] if resid else None)
+
+
+def wz_rational_minimax(power, lo, hi, d):
+    """Minimax relative approximation of x^power on [lo, hi] (host computation)."""
+    r = WzRational()
+    rc = LIB.wz_rational_minimax(float(power), float(lo), float(hi), int(d), ctypes.byref(r))
+    if rc != WZ_OK:
+        raise WzError(rc, "wz_rational_minimax failed")
+    return r
+
+
+def wz_spectral_bounds(ctx):
+    lo, hi = ctypes.c_double(), ctypes.c_double()
+    check(ctx, LIB.wz_spectral_bounds(ctx, ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def _as_rational(r):
+    return r if isinstance(r, WzRational) else rational_struct(r)
+
+
+def wz_rational_apply(ctx, r, inp, out, nrhs, tol=1e-10, maxiter=100000, flags=WZ_SOLVE_MIXED, pc_cutoff=100.0):
+    pin, _ = field_ptr(inp, WZ_C128)
+    pout, _ = field_ptr(out, WZ_C128)
+    st = WzSolveStats()
+    rr = _as_rational(r)
+    check(ctx, LIB.wz_rational_apply(ctx, ctypes.byref(rr), pin, pout, int(nrhs), float(tol), int(maxiter),
+                                     int(flags), float(pc_cutoff), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def wz_rhmc_force(ctx, eta, npf, action, grad, tol=1e-10, parts=WZ_FORCE_FERMION | WZ_FORCE_BOSON):
+    """grad <- dS/dphi with the rational action; returns (S_B, S_pf, solve stats)."""
+    pe = field_ptr(eta, WZ_C128)[0] if npf > 0 else ctypes.c_void_p(0)
+    pg, _ = field_ptr(grad, WZ_C128)
+    sb, spf, st = ctypes.c_double(), ctypes.c_double(), WzSolveStats()
+    ra = _as_rational(action)
+    check(ctx, LIB.wz_rhmc_force(ctx, pe, int(npf), ctypes.byref(ra), float(tol), int(parts), pg,
+                                 ctypes.byref(sb), ctypes.byref(spf), ctypes.byref(st)))
+    return sb.value, spf.value, st.as_dict()
+
+
+def wz_rhmc_trajectory(ctx, params, action, heatbath):
+    st = WzTrajStats()
+    ra, rh = _as_rational(action), _as_rational(heatbath)
+    check(ctx, LIB.wz_rhmc_trajectory(ctx, ctypes.byref(params), ctypes.byref(ra), ctypes.byref(rh),
+                                      ctypes.byref(st)))
+    return st.as_dict()
+
+
 def wz_aux_vev(ctx, nm=1):
     """(1/V) sum_x F~(x) per member, as a list of complex numbers."""
     out = (ctypes.c_double * (2 * nm))()
@@ -327,6 +435,23 @@ class Lattice:
 
     def get_phi(self, phi):
         return wz_get_phi(self.ctx, phi)
+
+    def solve_multishift(self, b, x, shifts, tol=1e-10, maxiter=100000, mixed=True, pc=False, resid=False):
+        flags = (WZ_SOLVE_MIXED if mixed else 0) | (WZ_SOLVE_PC if pc else 0)
+        return wz_solve_multishift(self.ctx, b, x, self._nrhs(b), shifts, tol, maxiter, flags, resid)
+
+    def spectral_bounds(self):
+        return wz_spectral_bounds(self.ctx)
+
+    def rational_apply(self, r, inp, out, tol=1e-10, maxiter=100000, mixed=True, pc=False, pc_cutoff=100.0):
+        flags = (WZ_SOLVE_MIXED if mixed else 0) | (WZ_SOLVE_PC if pc else 0)
+        return wz_rational_apply(self.ctx, r, inp, out, self._nrhs(inp), tol, maxiter, flags, pc_cutoff)
+
+    def rhmc_force(self, eta, npf, action, grad, tol=1e-10, parts=WZ_FORCE_FERMION | WZ_FORCE_BOSON):
+        return wz_rhmc_force(self.ctx, eta, npf, action, grad, tol, parts)
+
+    def rhmc_trajectory(self, action, heatbath, **kw):
+        return wz_rhmc_trajectory(self.ctx, hmc_params(**kw), action, heatbath)
 
     def aux_vev(self):
         return wz_aux_vev(self.ctx)[0]

@@ -233,6 +233,66 @@ static int apply_typed(wz_ctx* c, int op, const void* in, void* out, int nrhs, d
 
 using namespace wz;
 
+namespace wz {
+
+// Shared body of wz_solve and wz_solve_multishift: nb right-hand sides in b,
+// nsys systems (x has nsys fields), system q solves (M^dag M + sh.of(q)) x_q =
+// b[sh.src(q)].  Host buffers are staged through the context.
+static int solve_common(wz_ctx* c, const void* b, int nb, void* x, const ShiftSpec& sh, int nsys, double tol,
+                        int maxiter, unsigned flags, wz_solve_stats* stats, double* resid, const char* who) {
+  const std::string name(who);
+  if (!b || !x || nb < 0 || tol <= 0.0 || maxiter < 1) return set_error(c, WZ_EINVAL, name + ": bad argument");
+  if (b == x) return set_error(c, WZ_EINVAL, name + ": b and x must not alias");
+  if (c->nm > 1 && nb % c->nm) return set_error(c, WZ_EINVAL, name + ": nrhs must be a multiple of the members");
+  const auto t0 = std::chrono::steady_clock::now();
+  if (nsys == 0) {
+    if (stats) *stats = wz_solve_stats{};
+    return WZ_OK;
+  }
+  const size_t f1 = sizeof(cplx<double>) * 4 * (size_t)c->V;
+  const size_t fb = f1 * nb, fx = f1 * nsys;
+  const bool db = is_device_pointer(b), dx = is_device_pointer(x);
+  const cplx<double>* pb = (const cplx<double>*)b;
+  cplx<double>* px = (cplx<double>*)x;
+  if (!db || !dx) {
+    WZ_CUDA_TRY(c, c->ws_stage.reserve(fb + fx));
+    cplx<double>* sb = (cplx<double>*)c->ws_stage.ptr;
+    if (!db) {
+      WZ_CUDA_TRY(c, cudaMemcpyAsync(sb, b, fb, cudaMemcpyHostToDevice, c->stream));
+      pb = sb;
+    }
+    if (!dx) px = sb + 4L * c->V * nb;
+  }
+  const bool pc = (flags & WZ_SOLVE_PC) != 0;
+  if (pc && !c->same_mass) return set_error(c, WZ_EINVAL, name + ": M0^-1 preconditioning needs one mass for all members");
+  SolveOut o;
+  int rc = (flags & WZ_SOLVE_MIXED) ? solve_impl<float>(c, pb, px, nsys, sh, tol, maxiter, pc, 0.1, &o)
+                                    : solve_impl<double>(c, pb, px, nsys, sh, tol, maxiter, pc, 0.0, &o);
+  if (rc != WZ_OK && rc != WZ_NOT_CONVERGED) return rc;
+  if (resid) {
+    std::vector<double> rel(nsys);
+    int rc2 = true_residuals(c, pb, px, nsys, sh, rel.data());
+    if (rc2) return rc2;
+    memcpy(resid, rel.data(), sizeof(double) * nsys);
+  }
+  if (!dx) {
+    WZ_CUDA_TRY(c, cudaMemcpyAsync(x, px, fx, cudaMemcpyDeviceToHost, c->stream));
+  }
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (stats) {
+    stats->iterations = o.iterations;
+    stats->total_iterations = o.total_iterations;
+    stats->reliable_updates = o.reliable_updates;
+    stats->converged = o.converged;
+    stats->max_true_residual = o.max_true_residual;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (rc == WZ_NOT_CONVERGED) set_error(c, rc, name + ": maxiter reached before tol");
+  return rc;
+}
+
+}  // namespace wz
+
 extern "C" {
 
 int wz_supported_extent(int n) { return extent_supported(n) ? 1 : 0; }
@@ -300,8 +360,8 @@ int create_ctx(const wz_params* ps, int nm, void* stream, wz_ctx** out) {
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, WZ_PINNED_BYTES);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaMalloc(&c->counters, 4 * sizeof(unsigned long long));
-    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, 4 * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMalloc(&c->counters, WZ_NCOUNTERS * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(c->counters, 0, WZ_NCOUNTERS * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) rc = cuda_error(c, e, "create");
   }
@@ -355,6 +415,7 @@ int wz_destroy(wz_ctx* c) {
   c->ws_solver.release();
   c->ws_red.release();
   c->ws_force.release();
+  c->ws_rat.release();
   delete c;
   return WZ_OK;
 }
@@ -379,56 +440,26 @@ int wz_apply(wz_ctx* c, int op, int dtype, const void* in, void* out, int nrhs, 
 int wz_solve(wz_ctx* c, const void* b, void* x, int nrhs, double shift, double tol, int maxiter, unsigned flags,
              wz_solve_stats* stats, double* resid) {
   if (!c) return WZ_EINVAL;
-  if (!b || !x || nrhs < 0 || tol <= 0.0 || maxiter < 1 || shift < 0.0)
-    return set_error(c, WZ_EINVAL, "wz_solve: bad argument");
-  if (b == x) return set_error(c, WZ_EINVAL, "wz_solve: b and x must not alias");
-  if (c->nm > 1 && nrhs % c->nm) return set_error(c, WZ_EINVAL, "wz_solve: nrhs must be a multiple of the members");
-  if ((flags & WZ_SOLVE_PC) && shift != 0.0)
-    return set_error(c, WZ_EINVAL, "wz_solve: M0^-1 preconditioning is defined for shift = 0 only");
-  const auto t0 = std::chrono::steady_clock::now();
-  if (nrhs == 0) {
-    if (stats) *stats = wz_solve_stats{};
-    return WZ_OK;
+  if (shift < 0.0) return set_error(c, WZ_EINVAL, "wz_solve: bad argument");
+  return solve_common(c, b, nrhs, x, single_shift(shift), nrhs, tol, maxiter, flags, stats, resid, "wz_solve");
+}
+
+int wz_solve_multishift(wz_ctx* c, const void* b, void* x, int nrhs, int nshift, const double* shifts, double tol,
+                        int maxiter, unsigned flags, wz_solve_stats* stats, double* resid) {
+  if (!c) return WZ_EINVAL;
+  if (nshift < 1 || nshift > WZ_SHIFT_MAX || !shifts)
+    return set_error(c, WZ_EINVAL, "wz_solve_multishift: 1 <= nshift <= 64 shifts expected");
+  if (c->nm > 1 && nrhs % c->nm)
+    return set_error(c, WZ_EINVAL, "wz_solve_multishift: nrhs must be a multiple of the members");
+  ShiftSpec sh;
+  sh.d = nshift;
+  sh.inner = c->nm > 1 ? nrhs / c->nm : nrhs;
+  for (int i = 0; i < nshift; ++i) {
+    if (!(shifts[i] >= 0.0)) return set_error(c, WZ_EINVAL, "wz_solve_multishift: shifts must be >= 0");
+    sh.beta[i] = shifts[i];
   }
-  const size_t field = sizeof(cplx<double>) * 4 * (size_t)c->V * nrhs;
-  const bool db = is_device_pointer(b), dx = is_device_pointer(x);
-  const cplx<double>* pb = (const cplx<double>*)b;
-  cplx<double>* px = (cplx<double>*)x;
-  if (!db || !dx) {
-    WZ_CUDA_TRY(c, c->ws_stage.reserve(2 * field));
-    cplx<double>* sb = (cplx<double>*)c->ws_stage.ptr;
-    if (!db) {
-      WZ_CUDA_TRY(c, cudaMemcpyAsync(sb, b, field, cudaMemcpyHostToDevice, c->stream));
-      pb = sb;
-    }
-    if (!dx) px = sb + 4L * c->V * nrhs;
-  }
-  const bool pc = (flags & WZ_SOLVE_PC) != 0;
-  if (pc && !c->same_mass) return set_error(c, WZ_EINVAL, "wz_solve: M0^-1 preconditioning needs one mass for all members");
-  SolveOut o;
-  int rc = (flags & WZ_SOLVE_MIXED) ? solve_impl<float>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.1, &o)
-                                    : solve_impl<double>(c, pb, px, nrhs, shift, tol, maxiter, pc, 0.0, &o);
-  if (rc != WZ_OK && rc != WZ_NOT_CONVERGED) return rc;
-  if (resid) {
-    std::vector<double> rel(nrhs);
-    int rc2 = true_residuals(c, pb, px, nrhs, shift, rel.data());
-    if (rc2) return rc2;
-    memcpy(resid, rel.data(), sizeof(double) * nrhs);
-  }
-  if (!dx) {
-    WZ_CUDA_TRY(c, cudaMemcpyAsync(x, px, field, cudaMemcpyDeviceToHost, c->stream));
-  }
-  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  if (stats) {
-    stats->iterations = o.iterations;
-    stats->total_iterations = o.total_iterations;
-    stats->reliable_updates = o.reliable_updates;
-    stats->converged = o.converged;
-    stats->max_true_residual = o.max_true_residual;
-    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
-  }
-  if (rc == WZ_NOT_CONVERGED) set_error(c, rc, "wz_solve: maxiter reached before tol");
-  return rc;
+  if (nrhs == 0) sh.inner = 1;
+  return solve_common(c, b, nrhs, x, sh, nrhs * nshift, tol, maxiter, flags, stats, resid, "wz_solve_multishift");
 }
 
 unsigned long long wz_kernel_launches(void) { return g_launches.load(); }

@@ -13,14 +13,10 @@
 #include <vector>
 
 #include "apply_impl.cuh"
+#include "hmc.h"
 #include "solver.h"
 #include "wz_ctx.h"
 
-namespace wz {
-int force_impl(wz_ctx* c, const cplx<double>* eta, int npf, double tol, unsigned parts, cplx<double>* grad,
-               double* S_B, double* S_pf, SolveOut* so);
-int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st);
-}  // namespace wz
 
 using namespace wz;
 
@@ -146,9 +142,11 @@ int wz_batch_solve(wz_batch* b, const void* const* bs, void* const* xs, int nrhs
     }
     if (!rc)
       rc = (flags & WZ_SOLVE_MIXED)
-               ? solve_impl<float>(c, (const cplx<double>*)sb, (cplx<double>*)sx, nrhs * nm, 0.0, tol, maxiter,
+               ? solve_impl<float>(c, (const cplx<double>*)sb, (cplx<double>*)sx, nrhs * nm, single_shift(0.0), tol,
+                                   maxiter,
                                    false, 0.1, &outs[gi])
-               : solve_impl<double>(c, (const cplx<double>*)sb, (cplx<double>*)sx, nrhs * nm, 0.0, tol, maxiter,
+               : solve_impl<double>(c, (const cplx<double>*)sb, (cplx<double>*)sx, nrhs * nm, single_shift(0.0), tol,
+                                   maxiter,
                                     false, 0.0, &outs[gi]);
     if (rc == WZ_OK || rc == WZ_NOT_CONVERGED) {
       for (int j = 0; j < nm; ++j) {

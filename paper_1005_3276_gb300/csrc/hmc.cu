@@ -3,12 +3,17 @@
 // force(phi):  X_k = (M^dag M)^-1 eta_k   (one batched CG over the npf pseudofermions)
 //              G_k = site contraction of Z_k = M X_k with X_k         (xy_force)
 //              G   = G_B(phi) + sum_k G_k, S_B partials                (xy_boson_inv)
+// With a rational action (RHMC, Eq. jkjk) the solve holds d shifted systems
+// per pseudofermion, X_ik = (M^dag M + beta_i)^-1 eta_k, laid out
+// [member][pole][pseudofermion], and G_ik carries the weight alpha_i.
 // The leapfrog / Omelyan integrators and the Metropolis step follow Sec. 7.2;
 // the state (phi, pi) stays in FP64 on the device throughout.
 #include <chrono>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
+#include "hmc.h"
 #include "solver_impl.cuh"
 #include "wz_hmc.cuh"
 
@@ -22,9 +27,10 @@ static unsigned grid1d(long n) {
 // Workspace of the force / MD code (FP64), carved from ctx->ws_force.  Every
 // field carries the member index outermost; npf pseudofermions per member.
 struct ForceWS {
-  cplx<double>* X;     // [nm][npf][V][4] solutions
-  cplx<double>* A;     // [nm][npf][V][4] momentum intermediate
-  cplx<double>* Gk;    // [nm][npf][V] per-pseudofermion forces
+  cplx<double>* X;     // [nm][d][npf][V][4] solutions (d poles; 1 without a rational action)
+  cplx<double>* A;     // [nm][d][npf][V][4] momentum intermediate
+  cplx<double>* Gk;    // [nm][d][npf][V] per-system forces
+  cplx<double>* Y;     // [nm][npf][V][4] r(M^dag M) eta (rational action)
   cplx<double>* Bk;    // [nm][V][4] packed scalar field / its transform
   cplx<double>* G;     // [nm][V] total force
   cplx<double>* pi;    // [nm][V] momenta
@@ -43,7 +49,9 @@ struct ForceWS {
 
 static const int ND = 128;  // blocks of the dot-product partials per member
 
-static int force_ws(wz_ctx* c, int npf, ForceWS* w) {
+// npf pseudofermions; ds solutions per pseudofermion held at once (the larger
+// of the action's and the heatbath's pole counts), df of them in the force.
+static int force_ws(wz_ctx* c, int npf, ForceWS* w, int ds = 1, int df = 1) {
   const long nm = c->nm;
   const size_t f4 = sizeof(cplx<double>) * 4 * (size_t)c->V;
   const size_t f1 = sizeof(cplx<double>) * (size_t)c->V;
@@ -55,7 +63,8 @@ static int force_ws(wz_ctx* c, int npf, ForceWS* w) {
     off += (n + 255) & ~size_t(255);
     return r;
   };
-  const size_t oX = take(f4 * npf * nm), oA = take(f4 * npf * nm), oGk = take(f1 * npf * nm), oB = take(f4 * nm),
+  const size_t oX = take(f4 * npf * nm * ds), oA = take(f4 * npf * nm * df), oGk = take(f1 * npf * nm * df),
+               oY = take(f4 * npf * nm), oB = take(f4 * nm),
                oG = take(f1 * nm), oPi = take(f1 * nm), oP0 = take(f1 * nm), oR = take(f4 * npf * nm),
                oE = take(f4 * npf * nm), oParts = take(sizeof(double) * (6 * npart + 5 * nm + 8));
   WZ_CUDA_TRY(c, c->ws_force.reserve(off));
@@ -63,6 +72,7 @@ static int force_ws(wz_ctx* c, int npf, ForceWS* w) {
   w->X = (cplx<double>*)(b + oX);
   w->A = (cplx<double>*)(b + oA);
   w->Gk = (cplx<double>*)(b + oGk);
+  w->Y = (cplx<double>*)(b + oY);
   w->Bk = (cplx<double>*)(b + oB);
   w->G = (cplx<double>*)(b + oG);
   w->pi = (cplx<double>*)(b + oPi);
@@ -80,7 +90,27 @@ static int force_ws(wz_ctx* c, int npf, ForceWS* w) {
   return WZ_OK;
 }
 
+// A rational function on the device: pole shifts for the solver, residues for
+// the force weights and the combination; inner = pseudofermions per member.
+struct RatPoles {
+  ShiftSpec sh;
+  PoleSum ps;
+};
+
+static RatPoles make_poles(const wz_rational* r, int inner) {
+  RatPoles q;
+  q.sh.d = q.ps.d = r->d;
+  q.sh.inner = q.ps.inner = inner;
+  q.ps.a0 = r->a0;
+  for (int i = 0; i < r->d; ++i) {
+    q.sh.beta[i] = r->beta[i];
+    q.ps.alpha[i] = r->alpha[i];
+  }
+  return q;
+}
+
 struct ForceOpts {
+  const RatPoles* ra = nullptr;  // rational action (null: single pole, beta = 0)
   double tol = 1e-10;
   int maxiter = 100000;
   bool mixed = true;
@@ -99,10 +129,12 @@ static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int 
   const int nm = c->nm;
   cudaError_t e;
   int npf_eff = o.fermion ? npf : 0;
+  const int dpol = o.ra ? o.ra->ps.d : 1;  // systems per pseudofermion
   if (npf_eff > 0) {
-    const int nr = nm * npf;  // right-hand sides of the batched solve
-    int rc = o.mixed ? solve_impl<float>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.1, so, o.inline_capture)
-                     : solve_impl<double>(c, eta, w.X, nr, 0.0, o.tol, o.maxiter, false, 0.0, so, o.inline_capture);
+    const int nr = nm * npf * dpol;  // right-hand sides of the batched solve
+    const ShiftSpec sh = o.ra ? o.ra->sh : single_shift(0.0);
+    int rc = o.mixed ? solve_impl<float>(c, eta, w.X, nr, sh, o.tol, o.maxiter, false, 0.1, so, o.inline_capture)
+                     : solve_impl<double>(c, eta, w.X, nr, sh, o.tol, o.maxiter, false, 0.0, so, o.inline_capture);
     if (rc) return rc;
     // Z = M X without the site term: forward xy, +Dslash; the site term and the
     // contraction are fused into xy_force
@@ -121,7 +153,8 @@ static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int 
     fa.Gk = w.Gk;
     fa.phi = c->phi64;
     fa.kArr = c->k64;
-    fa.rpm = npf;
+    fa.rpm = npf * dpol;
+    if (o.ra) fa.pw = o.ra->ps;
     fa.Z = c->Z;
     fa.twc = c->t64.twc;
     fa.tws = c->t64.tws;
@@ -141,7 +174,7 @@ static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int 
   ba.A_out = w.Bk;
   ba.A = w.Bk;
   ba.Gk_in = w.Gk;
-  ba.npf = npf_eff;
+  ba.npf = npf_eff * dpol;
   ba.G = w.G;
   ba.part = sb_part;
   if (o.boson) {
@@ -158,6 +191,24 @@ static int force_eval(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int 
   }
   e = launch_fk(L, FK_BOSON_INV, ba, dim3(w.nb, nm), s);
   if (e != cudaSuccess) return cuda_error(c, e, "force: boson inverse");
+  return WZ_OK;
+}
+
+// partials [nm][ND] of the pseudofermion action from the solutions in w.X:
+// Re eta^dag X (single pole) or Re eta^dag (a0 eta + sum_i alpha_i X_i).
+static int pf_action_partials(wz_ctx* c, const ForceWS& w, const cplx<double>* eta, int npf, const RatPoles* ra,
+                              double* part) {
+  const long n4 = 4L * c->V;
+  const cplx<double>* y = w.X;
+  if (ra) {
+    count_launch();
+    pole_combine<<<dim3(64, c->nm * npf), 256, 0, c->stream>>>(eta, w.X, w.Y, n4, ra->ps);
+    WZ_CUDA_TRY(c, cudaGetLastError());
+    y = w.Y;
+  }
+  count_launch();
+  dot_re_partials<<<dim3(ND, c->nm), 256, 0, c->stream>>>(eta, y, n4 * npf, part);
+  WZ_CUDA_TRY(c, cudaGetLastError());
   return WZ_OK;
 }
 
@@ -179,8 +230,11 @@ static void add_solve(SolveOut& acc, const SolveOut& s) {
 
 // Molecular dynamics: phi (context) and w.pi evolve in place.  On return w.G,
 // w.X and w.sb1 belong to the final phi.  nforce counts force evaluations.
+// spf_first (may be null): pseudofermion-action partials from the first force
+// evaluation (the action at the starting phi).
 static int md_integrate(wz_ctx* c, ForceWS& w, const cplx<double>* eta, int npf, double tau, int nsteps,
-                        int integrator, const ForceOpts& o, SolveOut* acc, int* nforce, bool first_into_sb0) {
+                        int integrator, const ForceOpts& o, SolveOut* acc, int* nforce, bool first_into_sb0,
+                        double* spf_first = nullptr) {
   cudaStream_t s = c->stream;
   const long V = c->V * c->nm;  // all members' fields update together
   const double eps = tau / nsteps;
@@ -193,6 +247,7 @@ static int md_integrate(wz_ctx* c, ForceWS& w, const cplx<double>* eta, int npf,
     add_solve(*acc, one);
     ++*nforce;
     if (r == WZ_NOT_CONVERGED) return set_error(c, r, "force: solver did not converge");
+    if (!r && first && spf_first && npf > 0) r = pf_action_partials(c, w, eta, npf, o.ra, spf_first);
     return r;
   };
   auto P = [&](double h) {
@@ -246,11 +301,17 @@ static int host_member_sums(wz_ctx* c, const double* dev, int n, std::vector<dou
 
 // Forces and actions of every member.  eta: [nm][npf] fields (device).
 int force_impl(wz_ctx* c, const cplx<double>* eta, int npf, double tol, unsigned parts, cplx<double>* grad,
-               double* S_B, double* S_pf, SolveOut* so) {
+               double* S_B, double* S_pf, SolveOut* so, const wz_rational* ra) {
   ForceWS w;
-  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
+  const int dpol = ra ? ra->d : 1;
+  int rc = force_ws(c, npf > 0 ? npf : 1, &w, dpol, dpol);
   if (rc) return rc;
+  RatPoles rp;
   ForceOpts o;
+  if (ra) {
+    rp = make_poles(ra, npf);
+    o.ra = &rp;
+  }
   o.tol = tol;
   o.fermion = (parts & 1) != 0 && npf > 0;
   o.boson = (parts & 2) != 0;
@@ -269,10 +330,9 @@ int force_impl(wz_ctx* c, const cplx<double>* eta, int npf, double tol, unsigned
   }
   if (S_pf) {
     if (o.fermion) {
-      count_launch();
-      dot_re_partials<<<dim3(ND, c->nm), 256, 0, c->stream>>>(eta, w.X, 4L * c->V * npf, w.spf1);
-      WZ_CUDA_TRY(c, cudaGetLastError());
-      int r2 = host_member_sums(c, w.spf1, ND, v);
+      int r2 = pf_action_partials(c, w, eta, npf, o.ra, w.spf1);
+      if (r2) return r2;
+      r2 = host_member_sums(c, w.spf1, ND, v);
       if (r2) return r2;
       for (int j = 0; j < c->nm; ++j) S_pf[j] = v[j];
     } else {
@@ -286,8 +346,10 @@ int force_impl(wz_ctx* c, const cplx<double>* eta, int npf, double tol, unsigned
 // Enqueue one trajectory of every member (Sec. 7.2) on c->stream without any
 // host interaction in graph mode; the trajectory number is read on the device
 // from c->counters[3].  nf: force evaluations.
+// rh: heatbath rational function (RHMC; with o.ra) or null (eta = M^dag R).
+// body_h (may be null): kernels per trip of the captured heatbath solver loop.
 static int enqueue_trajectory(wz_ctx* c, ForceWS& w, const wz_hmc_params* h, const ForceOpts& o, SolveOut* acc,
-                              int* nf) {
+                              int* nf, const RatPoles* rh = nullptr, unsigned long long* body_h = nullptr) {
   const int npf = h->npf;
   const int nm = c->nm;
   cudaStream_t s = c->stream;
@@ -295,28 +357,57 @@ static int enqueue_trajectory(wz_ctx* c, ForceWS& w, const wz_hmc_params* h, con
   const unsigned g = grid1d(VN);
   const unsigned long long* trajp = c->counters + 3;
   int rc;
-  // heatbath: pi ~ N(0,1), R ~ exp(-|R|^2), eta = M^dag R
-  count_launch(2);
+  // heatbath: pi ~ N(0,1), R ~ exp(-|R|^2), eta = M^dag R (one pole) or
+  // eta = r_h(M^dag M) R (RHMC, Eq. hbeq)
+  count_launch();
   draw_momenta<<<g, 256, 0, s>>>(w.pi, V, nm, c->mid, h->seed, trajp);
   WZ_CUDA_TRY(c, cudaGetLastError());
   if (npf > 0) {
+    count_launch();
     draw_sources<<<grid1d(4 * VN * npf), 256, 0, s>>>(w.R, npf, V, nm, c->mid, h->seed, trajp);
     WZ_CUDA_TRY(c, cudaGetLastError());
-    rc = apply_op<double>(c, WZ_OP_MDAG, w.R, w.eta, npf * nm, 0.0, (cplx<double>*)c->ws_apply.ptr);
-    if (rc) return rc;
+    if (rh) {
+      SolveOut one;
+      c->trip_slot = 4;
+      rc = o.mixed ? solve_impl<float>(c, w.R, w.X, nm * npf * rh->sh.d, rh->sh, o.tol, o.maxiter, false, 0.1, &one,
+                                       o.inline_capture)
+                   : solve_impl<double>(c, w.R, w.X, nm * npf * rh->sh.d, rh->sh, o.tol, o.maxiter, false, 0.0, &one,
+                                        o.inline_capture);
+      c->trip_slot = 2;
+      if (body_h) *body_h = c->inline_body_launches;
+      add_solve(*acc, one);
+      if (rc == WZ_NOT_CONVERGED) return set_error(c, rc, "heatbath: solver did not converge");
+      if (rc) return rc;
+      count_launch();
+      pole_combine<<<dim3(64, nm * npf), 256, 0, s>>>(w.R, w.X, w.eta, 4L * V, rh->ps);
+      WZ_CUDA_TRY(c, cudaGetLastError());
+    } else {
+      rc = apply_op<double>(c, WZ_OP_MDAG, w.R, w.eta, npf * nm, 0.0, (cplx<double>*)c->ws_apply.ptr);
+      if (rc) return rc;
+    }
   }
   WZ_CUDA_TRY(c, cudaMemcpyAsync(w.phi0, c->phi64, sizeof(cplx<double>) * VN, cudaMemcpyDeviceToDevice, s));
-  count_launch(2);
+  count_launch();
   dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.pi, w.pi, V, w.kin0);
-  if (npf > 0) dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.R, w.R, 4L * V * npf, w.spf0);
-  else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf0, 0, ND * nm * sizeof(double), s));
+  if (npf > 0 && !o.ra) {  // eta^dag (M^dag M)^-1 eta = |R|^2 exactly
+    count_launch();
+    dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.R, w.R, 4L * V * npf, w.spf0);
+  } else if (npf == 0) {
+    WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf0, 0, ND * nm * sizeof(double), s));
+  }
   WZ_CUDA_TRY(c, cudaGetLastError());
-  rc = md_integrate(c, w, w.eta, npf, h->tau, h->nsteps, h->integrator, o, acc, nf, true);
+  // RHMC: S_pf at the start from the solves of the first force evaluation
+  rc = md_integrate(c, w, w.eta, npf, h->tau, h->nsteps, h->integrator, o, acc, nf, true,
+                    (npf > 0 && o.ra) ? w.spf0 : nullptr);
   if (rc) return rc;
-  count_launch(2);
+  count_launch();
   dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.pi, w.pi, V, w.kin1);
-  if (npf > 0) dot_re_partials<<<dim3(ND, nm), 256, 0, s>>>(w.eta, w.X, 4L * V * npf, w.spf1);
-  else WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf1, 0, ND * nm * sizeof(double), s));
+  if (npf > 0) {
+    rc = pf_action_partials(c, w, w.eta, npf, o.ra, w.spf1);
+    if (rc) return rc;
+  } else {
+    WZ_CUDA_TRY(c, cudaMemsetAsync(w.spf1, 0, ND * nm * sizeof(double), s));
+  }
   HParts hp{w.kin0, ND, w.sb0, w.nb, w.spf0, ND, w.kin1, ND, w.sb1, w.nb, w.spf1, ND};
   count_launch(2);
   metropolis<<<(nm + 31) / 32, 32, 0, s>>>(hp, w.res, nm, c->mid, h->seed, trajp);
@@ -333,15 +424,44 @@ static int enqueue_trajectory(wz_ctx* c, ForceWS& w, const wz_hmc_params* h, con
 // solver loop as a WHILE conditional node, the updates, H and the Metropolis
 // decisions -- is one CUDA graph, captured once per parameter set and then
 // replayed (the trajectory number is written to the device before a replay).
-int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
+// FNV-1a over the coefficients of the rational action and heatbath (graph key)
+static unsigned long long rational_hash(const wz_rational* ra, const wz_rational* rh) {
+  unsigned long long hsh = 1469598103934665603ULL;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = (const unsigned char*)p;
+    for (size_t i = 0; i < n; ++i) hsh = (hsh ^ b[i]) * 1099511628211ULL;
+  };
+  for (const wz_rational* r : {ra, rh}) {
+    if (!r) {
+      mix("-", 1);
+      continue;
+    }
+    mix(&r->d, sizeof(r->d));
+    mix(&r->a0, sizeof(r->a0));
+    mix(r->alpha, sizeof(double) * r->d);
+    mix(r->beta, sizeof(double) * r->d);
+  }
+  return hsh;
+}
+
+// ra, rh: rational action and heatbath (RHMC), both or neither.
+int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st, const wz_rational* ra,
+                    const wz_rational* rh) {
   const auto t0 = std::chrono::steady_clock::now();
   const int npf = h->npf;
   const int nm = c->nm;
+  const int da = ra ? ra->d : 1, dh = rh ? rh->d : 1;
   ForceWS w;
-  int rc = force_ws(c, npf > 0 ? npf : 1, &w);
+  int rc = force_ws(c, npf > 0 ? npf : 1, &w, da > dh ? da : dh, da);
   if (rc) return rc;
-  if (npf > 0) WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAG, npf * nm)));
+  if (npf > 0 && !rh) WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAG, npf * nm)));
+  RatPoles rpa, rph;
   ForceOpts o;
+  if (ra) {
+    rpa = make_poles(ra, npf);
+    rph = make_poles(rh, npf);
+    o.ra = &rpa;
+  }
   o.tol = h->tol;
   o.maxiter = h->maxiter > 0 ? h->maxiter : 100000;
   o.mixed = (h->flags & WZ_HMC_FP64_SOLVES) == 0;
@@ -351,18 +471,19 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
   unsigned long long* hc = (unsigned long long*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
   if (sizeof(double) * 5 * nm + 64 > WZ_PINNED_BYTES - WZ_PINNED_SCRATCH_OFFSET)
     return set_error(c, WZ_EINVAL, "too many members");
-  double* hres = (double*)(hc + 8);
+  double* hres = (double*)(hc + WZ_NCOUNTERS);
   // device state of this trajectory: counters zero, trajectory number
-  hc[0] = hc[1] = hc[2] = 0;
+  for (int i = 0; i < WZ_NCOUNTERS; ++i) hc[i] = 0;
   hc[3] = h->traj_index;
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(c->counters, hc, 4 * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(c->counters, hc, WZ_NCOUNTERS * sizeof(unsigned long long), cudaMemcpyHostToDevice, s));
   const bool graph = c->use_graphs && !g_probe.active;
   if (graph) {
     // reserve the solver workspace now: nothing may allocate during the capture
     {
       const int nblk = xy_nblk(c->X, c->T * c->Z);
-      SolverWS<float> W1(c->V, nm * (npf > 0 ? npf : 1), nblk, false);
-      SolverWS<double> W2(c->V, nm * (npf > 0 ? npf : 1), nblk, false);
+      const int nsys = nm * (npf > 0 ? npf : 1) * (da > dh ? da : dh);
+      SolverWS<float> W1(c->V, nsys, nblk, false);
+      SolverWS<double> W2(c->V, nsys, nblk, false);
       WZ_CUDA_TRY(c, c->ws_solver.reserve(o.mixed ? W1.total : W2.total));
     }
     TrajGraphKey key{};
@@ -374,6 +495,7 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
     key.maxiter = o.maxiter;
     key.flags = h->flags;
     key.seed = h->seed;
+    key.rational = rational_hash(ra, rh);
     key.ws_force = c->ws_force.ptr;
     key.ws_solver = c->ws_solver.ptr;
     key.ws_apply = c->ws_apply.ptr;
@@ -390,12 +512,15 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
       ForceOpts oc = o;
       oc.inline_capture = true;
       cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeRelaxed);
-      int rc2 = e == cudaSuccess ? enqueue_trajectory(c, w, h, oc, &acc, &nf) : WZ_ECUDA;
+      unsigned long long body_h = 0;
+      int rc2 = e == cudaSuccess ? enqueue_trajectory(c, w, h, oc, &acc, &nf, ra ? &rph : nullptr, &body_h)
+                                 : WZ_ECUDA;
       cudaGraph_t gr = nullptr;
       cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &gr);
       c->stream = saved;
       T.outer_launches = tl_launches - l0;
       T.body_launches = c->inline_body_launches;
+      T.body_launches_h = body_h;
       g_launches -= T.outer_launches;
       tl_launches = l0;
       if (e != cudaSuccess) return cuda_error(c, e, "trajectory capture");
@@ -412,13 +537,15 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {
     WZ_CUDA_TRY(c, cudaGraphLaunch(T.exec, s));
     nf = T.force_evals;
   } else {
-    rc = enqueue_trajectory(c, w, h, o, &acc, &nf);
+    rc = enqueue_trajectory(c, w, h, o, &acc, &nf, ra ? &rph : nullptr);
     if (rc) return rc;
   }
   WZ_CUDA_TRY(c, cudaMemcpyAsync(hres, w.res, 5 * nm * sizeof(double), cudaMemcpyDeviceToHost, s));
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(hc, c->counters, 4 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(hc, c->counters, WZ_NCOUNTERS * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
   WZ_CUDA_TRY(c, cudaStreamSynchronize(s));
-  if (graph) count_launch(c->traj_graph.outer_launches + hc[2] * c->traj_graph.body_launches);
+  if (graph)
+    count_launch(c->traj_graph.outer_launches + hc[2] * c->traj_graph.body_launches +
+                 hc[4] * c->traj_graph.body_launches_h);
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int j = 0; st && j < nm; ++j) {
     st[j].H0 = hres[5 * j + 0];
@@ -504,6 +631,51 @@ int wz_md_integrate(wz_ctx* c, void* pi, const void* eta, int npf, const wz_hmc_
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return WZ_OK;
+}
+
+static bool rational_ok(const wz_rational* r) {
+  if (!r || r->d < 1 || r->d > WZ_RATIONAL_MAX) return false;
+  for (int i = 0; i < r->d; ++i)
+    if (!(r->beta[i] >= 0.0) || !std::isfinite(r->alpha[i])) return false;
+  return std::isfinite(r->a0);
+}
+
+int wz_rhmc_force(wz_ctx* c, const void* eta, int npf, const wz_rational* action, double tol, unsigned parts,
+                  void* grad, double* S_B, double* S_pf, wz_solve_stats* stats) {
+  if (!c) return WZ_EINVAL;
+  if (!grad || npf < 0 || (npf > 0 && !eta) || tol <= 0.0 || !rational_ok(action))
+    return set_error(c, WZ_EINVAL, "wz_rhmc_force: bad argument");
+  if (c->nm != 1) return set_error(c, WZ_EINVAL, "wz_rhmc_force: single-lattice context expected");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t f4 = sizeof(cplx<double>) * 4 * (size_t)c->V;
+  const cplx<double>* e = (const cplx<double>*)eta;
+  if (npf > 0 && !is_device_pointer(eta)) {
+    WZ_CUDA_TRY(c, c->ws_stage.reserve(f4 * npf));
+    WZ_CUDA_TRY(c, cudaMemcpyAsync(c->ws_stage.ptr, eta, f4 * npf, cudaMemcpyHostToDevice, c->stream));
+    e = (const cplx<double>*)c->ws_stage.ptr;
+  }
+  SolveOut so;
+  int rc = force_impl(c, e, npf, tol, parts, (cplx<double>*)grad, S_B, S_pf, &so, action);
+  if (rc && rc != WZ_NOT_CONVERGED) return rc;
+  if (stats) {
+    stats->iterations = so.iterations;
+    stats->total_iterations = so.total_iterations;
+    stats->reliable_updates = so.reliable_updates;
+    stats->converged = so.converged;
+    stats->max_true_residual = so.max_true_residual;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return rc;
+}
+
+int wz_rhmc_trajectory(wz_ctx* c, const wz_hmc_params* h, const wz_rational* action, const wz_rational* heatbath,
+                       wz_traj_stats* st) {
+  if (!c) return WZ_EINVAL;
+  if (!h || h->npf < 1 || h->nsteps < 1 || h->tol <= 0.0 || h->tau <= 0.0 || !rational_ok(action) ||
+      !rational_ok(heatbath))
+    return set_error(c, WZ_EINVAL, "wz_rhmc_trajectory: bad argument");
+  if (c->nm != 1) return set_error(c, WZ_EINVAL, "wz_rhmc_trajectory: single-lattice context expected");
+  return trajectory_impl(c, h, st, action, heatbath);
 }
 
 int wz_trajectory(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st) {

@@ -107,7 +107,7 @@ static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st
   switch (MODE) {
     case CG_P1: site = 6 * f; kind = PK_CG_P1; break;                 // r, p, x in; p, A, x out
     case CG_P3: site = 4 * f + ph; kind = PK_CG_P3; break;            // A, p in; C, A out; phi
-    case CG_P5: site = (a.shift != 0.0 ? 5 : 4) * f + (PC ? 0 : ph); kind = PK_CG_P5; break;  // A, C, r (p) in; r out
+    case CG_P5: site = (a.shifted && !PC ? 5 : 4) * f + (PC ? 0 : ph); kind = PK_CG_P5; break;  // A, C, r (p) in; r out
     case RU_P1: site = 3 * f + 3 * lo; kind = PK_RU_P1; break;        // x_hi, x_lo, p in; x_hi, x_lo, A out
     case RU_P5: site = 4 * f + lo + (PC ? 0 : ph); kind = PK_RU_P5; break;  // A, x_hi, C, b in; r out
   }

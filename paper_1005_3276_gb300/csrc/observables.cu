@@ -55,6 +55,28 @@ static __global__ void locality_max(const cplx<double>* psi, int T, int Z, int Y
   }
 }
 
+// min / max over the momenta of den(p) = D_mu^dag D_mu + |m|^2 = 1 / (dV V)
+// (positive, so the IEEE bit patterns order like the values).
+static __global__ void den_minmax(const double* dV, long V, unsigned long long* mm) {
+  double lo = HUGE_VAL, hi = 0.0;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < V; i += (long)gridDim.x * blockDim.x) {
+    const double den = 1.0 / (dV[i] * (double)V);
+    lo = fmin(lo, den);
+    hi = fmax(hi, den);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+    hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    unsigned long long bl, bh;
+    memcpy(&bl, &lo, sizeof(bl));
+    memcpy(&bh, &hi, sizeof(bh));
+    atomicMin(&mm[0], bl);
+    atomicMax(&mm[1], bh);
+  }
+}
+
 }  // namespace wz
 
 using namespace wz;
@@ -109,6 +131,28 @@ int wz_locality(wz_ctx* c, double* f, int nf) {
   WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   for (int r = 0; r <= rmax; ++r) memcpy(&f[r], &h[r], sizeof(double));
   for (int r = rmax + 1; r < nf; ++r) f[r] = 0.0;
+  return WZ_OK;
+}
+
+int wz_spectral_bounds(wz_ctx* c, double* lo, double* hi) {
+  if (!c || !lo || !hi) return set_error(c, WZ_EINVAL, "wz_spectral_bounds: null pointer");
+  WZ_CUDA_TRY(c, c->ws_red.reserve(2 * sizeof(unsigned long long)));
+  unsigned long long* mm = (unsigned long long*)c->ws_red.ptr;
+  const double inf = HUGE_VAL;
+  unsigned long long init[2] = {0, 0};
+  memcpy(&init[0], &inf, sizeof(double));
+  unsigned long long* h = (unsigned long long*)((char*)c->host_pinned + WZ_PINNED_SCRATCH_OFFSET);
+  h[0] = init[0];
+  h[1] = init[1];
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(mm, h, 2 * sizeof(unsigned long long), cudaMemcpyHostToDevice, c->stream));
+  count_launch();
+  const long blocks = (c->V + 255) / 256;
+  den_minmax<<<(unsigned)(blocks < 1024 ? blocks : 1024), 256, 0, c->stream>>>(c->t64.dV, c->V, mm);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(h, mm, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, c->stream));
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  memcpy(lo, &h[0], sizeof(double));
+  memcpy(hi, &h[1], sizeof(double));
   return WZ_OK;
 }
 

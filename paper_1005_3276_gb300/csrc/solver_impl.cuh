@@ -49,9 +49,10 @@ template <typename RI> struct SolverWS {
 };
 
 // b, x: FP64 device fields.  RI: iteration precision (float: mixed, double: FP64).
+// nrhs systems; system q solves (M^dag M + sh.of(q)) x_q = b[sh.src(q)].
 template <typename RI>
-int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, double shift, double tol, int maxiter,
-               bool pc, double delta, SolveOut* out, bool inline_capture) {
+int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, const ShiftSpec& sh, double tol,
+               int maxiter, bool pc, double delta, SolveOut* out, bool inline_capture) {
   if (inline_capture && pc) return set_error(c, WZ_EINVAL, "preconditioned solves cannot be captured inline");
   const int L = c->X;
   const int TZ = c->T * c->Z;
@@ -77,18 +78,19 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   // preconditioned problem: b~ = (M0^-1)^dag b, solve for x~ = M0 x
   cplx<double>* bs = (cplx<double>*)(base + W.off_bt);
   cplx<double>* xs = (cplx<double>*)(base + W.off_xt);
+  count_launch();
+  gather_rhs<<<dim3(64, nrhs), 256, 0, s>>>(b, bs, n_per_rhs, sh);
+  WZ_CUDA_TRY(c, cudaGetLastError());
   if (pc) {
-    int rc = apply_op<double>(c, WZ_OP_M0INV_DAG, b, bs, nrhs, 0.0, A64);
+    int rc = apply_op<double>(c, WZ_OP_M0INV_DAG, bs, bs, nrhs, 0.0, A64);
     if (rc) return rc;
-  } else {
-    WZ_CUDA_TRY(c, cudaMemcpyAsync(bs, b, W.field64, cudaMemcpyDeviceToDevice, s));
   }
 
   WZ_CUDA_TRY(c, cudaMemsetAsync(xs, 0, W.field64, s));
   count_launch(2);
   cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, p, n_per_rhs, partR, 64);
   WZ_CUDA_TRY(c, cudaGetLastError());
-  cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol);
+  cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol, sh);
   WZ_CUDA_TRY(c, cudaGetLastError());
 
   const int gate_stride = sizeof(RhsState) / sizeof(int);
@@ -107,7 +109,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   ga.Z = c->Z;
   ga.twc = tables<RI>(c).twc;
   ga.tws = tables<RI>(c).tws;
-  ga.shift = shift;
+  ga.shifted = sh.any();
   ga.st = st;
   ga.nblk = nblk;
   ga.TZ = TZ;
@@ -127,7 +129,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   ra.Z = c->Z;
   ra.twc = c->t64.twc;
   ra.tws = c->t64.tws;
-  ra.shift = shift;
+  ra.shifted = ga.shifted;
   ra.st = st;
   ra.nblk = nblk;
   ra.TZ = TZ;
@@ -161,6 +163,9 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   // chosen per solve shape by timing the candidates (autotune_group below).
   int gsz = nrhs;
 
+  // iteration counters of the chunks (off while the tuner times candidates)
+  unsigned long long* cnt = c->counters;
+
   // one chunk: K iterations and one reliable-update block, all gated on the device
   auto issue_chunk = [&](cudaStream_t q) -> cudaError_t {
     cudaError_t e2;
@@ -192,7 +197,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
         WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, ng, q));
       }
       count_launch();
-      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter, c->counters);
+      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter, cnt);
       WZ_Q(cudaGetLastError());
     }
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P1, ra, nrhs, q));
@@ -207,7 +212,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     r3.Z = c->Z;
     r3.twc = c->t64.twc;
     r3.tws = c->t64.tws;
-    r3.shift = shift;
+    r3.shifted = ga.shifted;
     r3.st = st;
     r3.nblk = nblk;
     r3.TZ = TZ;
@@ -218,7 +223,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     r5.part_out = partR;
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, q));
     count_launch();
-    cg_scalar_ru<<<nrhs, 32, 0, q>>>(st, partR, nblk, maxiter, c->counters);
+    cg_scalar_ru<<<nrhs, 32, 0, q>>>(st, partR, nblk, maxiter, cnt);
     WZ_Q(cudaGetLastError());
 #undef WZ_Q
     return cudaSuccess;
@@ -250,6 +255,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
           if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
         }
       cudaEvent_t e0, e1;
+      cnt = nullptr;
       WZ_RUN(cudaEventCreate(&e0));
       WZ_RUN(cudaEventCreate(&e1));
       float best = 1e30f;
@@ -273,11 +279,12 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
         count_launch(2);
         cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, p, n_per_rhs, partR, 64);
         WZ_RUN(cudaGetLastError());
-        cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol);
+        cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol, sh);
         WZ_RUN(cudaGetLastError());
       }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
+      cnt = c->counters;
       gsz = bestg;
       std::lock_guard<std::mutex> lk(mu);
       cache[tkey] = gsz;
@@ -291,7 +298,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   // cached on the context and replayed by every solve of the same shape.
   // The kernel probe needs eager launches (it brackets each launch).
   const bool use_graph = c->use_graphs && !g_probe.active;
-  SolverGraph& G = c->solver_graph[sizeof(RI) == 4 ? 0 : 1];
+  SolverGraph& G = c->solver_graph[(sizeof(RI) == 4 ? 0 : 1) + (pc ? 2 : 0)];
   int* trips = (int*)(base + W.off_trips);
 
   // Inline capture: the caller is capturing stream s into a larger graph (a
@@ -320,7 +327,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     cudaError_t ce = issue_chunk(c->cap_stream2);
     if (ce == cudaSuccess) {
       count_launch();
-      cg_loop_cond<<<1, 32, 0, c->cap_stream2>>>(h, st, nrhs, trips, max_chunks, c->counters);
+      cg_loop_cond<<<1, 32, 0, c->cap_stream2>>>(h, st, nrhs, trips, max_chunks, c->counters, c->trip_slot);
       ce = cudaGetLastError();
     }
     c->inline_body_launches = tl_launches - l0;
@@ -339,7 +346,6 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
     SolverGraphKey key{};
     key.nrhs = nrhs;
     key.pc = pc;
-    key.shift = shift;
     key.maxiter = maxiter;
     key.delta2 = delta2;
     key.ws = c->ws_solver.ptr;
@@ -366,7 +372,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
       cudaError_t ce = issue_chunk(c->cap_stream);
       if (ce == cudaSuccess) {
         count_launch();
-        cg_loop_cond<<<1, 32, 0, c->cap_stream>>>(h, st, nrhs, trips, max_chunks, c->counters);
+        cg_loop_cond<<<1, 32, 0, c->cap_stream>>>(h, st, nrhs, trips, max_chunks, c->counters, 2);
         ce = cudaGetLastError();
       }
       G.body_launches = tl_launches - l0;  // kernels per trip of the WHILE body
@@ -411,7 +417,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, doub
   {
     int rc = apply_op<double>(c, WZ_OP_M0INV, xs, x, nrhs, 0.0, A64);
     if (rc) return rc;
-    rc = true_residuals(c, b, x, nrhs, shift, rel.data());
+    rc = true_residuals(c, b, x, nrhs, sh, rel.data());
     if (rc) return rc;
   }
   bool again = false;

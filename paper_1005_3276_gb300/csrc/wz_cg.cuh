@@ -13,6 +13,14 @@
 //            partial |r|^2
 //   S        rr_new, beta = rr_new / rr, reliable-update and stop tests
 //
+// sigma is a property of each right-hand side (RhsState::shift): the d shifted
+// systems (M^dag M + beta_i) X_i = eta of a rational approximation (Eq. jkjk,
+// Eq. yuier) run as d right-hand sides of one solve.  Preconditioned, the
+// shifted operator is M~^dag M~ + sigma M0^-1^dag M0^-1 (the form Sec. 7.4 gives
+// for Eq. yuier): with u = M0^-1 p in position space, P3 forms C = p + Y u,
+// adds sigma |u|^2 to p.Ap and transforms Y^dag C + sigma u, so that P5's
+// C + M0^-1^dag(Y^dag C + sigma u) is the whole operator.
+//
 // p.Ap = |M p|^2 + sigma |p|^2 is known after P3, so P5 updates r without
 // storing Ap; the x update of an iteration is deferred to the next P1, which
 // reads p anyway (or to the reliable update, which folds it in).  Reductions are deterministic: per-thread
@@ -32,6 +40,7 @@
 // The pure FP64 solver is the same code with FP64 iteration vectors and
 // delta = 0 (the update then only runs as the final true-residual check).
 #pragma once
+#include "../../include/wz.h"
 #include "wz_kernels.cuh"
 
 // blocks per SM the CG passes are compiled for (85 registers a thread at 256
@@ -51,6 +60,7 @@ struct RhsState {
   double rtrue2;   // |b - A x|^2 at the last reliable update (FP64)
   double tol2;     // stop when |b - A x|^2 <= tol2 |b|^2
   double alpha;    // alpha of the last iteration, whose x += alpha p is still pending
+  double shift;    // sigma of this system: A = M^dag M + sigma
   int run;         // iteration passes act on this RHS
   int ru;          // reliable update pending
   int active;      // not finished
@@ -77,7 +87,7 @@ template <typename R, typename LO> struct CGArgs {
   int Z;                // planes per time slice (plane = t * Z + z)
   const R* twc;         // cos / sin (pi t / T): antiperiodic twist (see xy_pass)
   const R* tws;
-  double shift;
+  int shifted;          // some right-hand side has sigma != 0 (probe byte counts only)
   RhsState* st;
   double* part_out;     // [rhs][nblk] block partials written by this pass (may be null)
   const double* part_in;  // [rhs][nblk] block partials of p.Ap (CG_P5)
@@ -138,6 +148,7 @@ xy_cg(CGArgs<R, LO> a) {
   const int rhs = blockIdx.y + a.rhs0;
   RhsState* st = a.st + rhs;
   if (!(a.gate_ru ? st->ru : st->run)) return;  // whole block, before any barrier
+  const double shift = st->shift;
 
   const int tid = threadIdx.x;
   if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
@@ -165,7 +176,7 @@ xy_cg(CGArgs<R, LO> a) {
     constexpr unsigned PB = L * L * 4 * sizeof(cplx<R>);
     const long pe = plane * (long)(L * L) * 4;
     if constexpr (MODE == CG_P5) {
-      if (a.shift != 0.0) prefetch_l2(Pp + pe, PB);
+      if (!PC && shift != 0.0) prefetch_l2(Pp + pe, PB);
       prefetch_l2(Pc + pe, PB);
       prefetch_l2(Pr + pe, PB);
     } else if constexpr (MODE == CG_P3) {
@@ -196,7 +207,7 @@ xy_cg(CGArgs<R, LO> a) {
     alpha = (R)st->alpha;  // pending x update of the previous iteration
   }
   const double alpha_pending = (MODE == RU_P1) ? st->alpha : 0.0;
-  const R sigma = (R)a.shift;
+  const R sigma = (R)shift;
 
   if (live) {
     const int x = w;
@@ -227,16 +238,23 @@ xy_cg(CGArgs<R, LO> a) {
       } else if constexpr (MODE == CG_P3) {
         const cplx<R> pe = Pp[e];
         const cplx<R> f = a.phi[phib + y * L];
-        if constexpr (PC) v[y] = pe + site_coef<R, false, false>(kc, f, s) * v[y];
-        else v[y] = v[y] + site_coef<R, false, true>(kc, f, s) * pe;
-        Pc[e] = v[y];
-        part += norm2(v[y]) + sigma * norm2(pe);
-        if constexpr (PC) v[y] = site_coef<R, true, false>(kc, f, s) * v[y];
+        if constexpr (PC) {
+          const cplx<R> u = v[y];  // M0^-1 p
+          const cplx<R> cv = pe + site_coef<R, false, false>(kc, f, s) * u;
+          Pc[e] = cv;
+          part += norm2(cv) + sigma * norm2(u);
+          v[y] = site_coef<R, true, false>(kc, f, s) * cv;
+          if (sigma != R(0)) v[y] = v[y] + sigma * u;
+        } else {
+          v[y] = v[y] + site_coef<R, false, true>(kc, f, s) * pe;
+          Pc[e] = v[y];
+          part += norm2(v[y]) + sigma * norm2(pe);
+        }
       } else if constexpr (MODE == CG_P5 || MODE == RU_P5) {
         cplx<R> ap;
         if constexpr (PC) ap = Pc[e] + v[y];
         else ap = v[y] + site_coef<R, true, true>(kc, a.phi[phib + y * L], s) * Pc[e];
-        if (sigma != R(0)) ap = ap + sigma * Pp[e];  // p, or x_hi for RU_P5
+        if (!PC && sigma != R(0)) ap = ap + sigma * Pp[e];  // p, or x_hi for RU_P5
         if constexpr (MODE == CG_P5) {
           const cplx<R> rn = Pr[e] - alpha * ap;
           Pr[e] = rn;
@@ -290,8 +308,36 @@ __global__ void cg_init(const cplx<double>* b, cplx<R>* r, cplx<R>* x, cplx<R>* 
   if (threadIdx.x == 0) part[(long)rhs * nblk + blockIdx.x] = t;
 }
 
+// Shifts of the systems of one solve, passed by value (so that a captured
+// solve carries them): system q solves (M^dag M + beta[(q / inner) % d]) x = b.
+// A plain solve has d = 1; the d poles of a rational approximation applied to
+// npf right-hand sides per member are laid out [member][pole][rhs] (inner = npf).
+#define WZ_SHIFT_MAX 64
+struct ShiftSpec {
+  int d = 1;
+  int inner = 1;
+  double beta[WZ_SHIFT_MAX] = {0.0};
+  __host__ __device__ double of(int q) const { return beta[(q / inner) % d]; }
+  // right-hand side (input field) of system q: [member][rhs] without the pole index
+  __host__ __device__ long src(int q) const { return (long)(q / (inner * d)) * inner + q % inner; }
+  bool any() const {
+    for (int i = 0; i < d; ++i)
+      if (beta[i] != 0.0) return true;
+    return false;
+  }
+};
+
+// bs[q] = b[sh.src(q)]: the right-hand side of every shifted system.  Grid (nb, nsys).
+static __global__ void gather_rhs(const cplx<double>* b, cplx<double>* bs, long n_per_rhs, ShiftSpec sh) {
+  const int q = blockIdx.y;
+  const cplx<double>* src = b + sh.src(q) * n_per_rhs;
+  cplx<double>* dst = bs + (long)q * n_per_rhs;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n_per_rhs; i += (long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
 // One warp per RHS.
-static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk, double tol2) {
+static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk, double tol2, ShiftSpec sh) {
   RhsState* s = st + blockIdx.x;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
   if (threadIdx.x == 0) {
@@ -303,6 +349,7 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
     s->rtrue2 = t;
     s->tol2 = tol2;
     s->alpha = 0.0;
+    s->shift = sh.of(blockIdx.x);
     s->iters = 0;
     s->ru_count = 0;
     s->ru = 0;
@@ -366,12 +413,12 @@ static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, 
 // Condition of the solver graph's WHILE node: continue while some RHS is
 // active, and never beyond cap trips.
 static __global__ void cg_loop_cond(cudaGraphConditionalHandle h, const RhsState* st, int nrhs, int* trips, int cap,
-                                    unsigned long long* counters) {
+                                    unsigned long long* counters, int slot) {
   if (threadIdx.x != 0) return;
   int any = 0;
   for (int j = 0; j < nrhs; ++j) any |= st[j].active;
   const int t = ++*trips;
-  if (counters) counters[2] += 1ULL;
+  if (counters) counters[slot] += 1ULL;
   cudaGraphSetConditional(h, (any && t < cap) ? 1u : 0u);
 }
 

@@ -54,7 +54,6 @@ struct DevBuf {
 struct SolverGraphKey {
   int nrhs;
   int pc;
-  double shift;
   int maxiter;
   double delta2;
   void* ws;
@@ -83,6 +82,7 @@ struct TrajGraphKey {
   int nsteps, integrator, npf, maxiter;
   unsigned flags;
   unsigned long long seed;
+  unsigned long long rational;  // hash of the rational action and heatbath (RHMC), else of none
   void *ws_force, *ws_solver, *ws_apply;
   size_t b_force, b_solver, b_apply;
 };
@@ -90,7 +90,7 @@ struct TrajGraph {
   TrajGraphKey key{};
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  unsigned long long outer_launches = 0, body_launches = 0;
+  unsigned long long outer_launches = 0, body_launches = 0, body_launches_h = 0;
   int force_evals = 0;
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -128,20 +128,26 @@ struct wz_ctx {
   wz::DevBuf ws_solver;   // solver vectors
   wz::DevBuf ws_red;      // reduction partials and per-RHS scalars
   wz::DevBuf ws_force;    // force / HMC fields
+  wz::DevBuf ws_rat;      // shifted solutions of a rational apply
   // small pinned block for scalar read-back: [0, WZ_PINNED_SCRATCH_OFFSET) holds
   // the solver's per-RHS state, the rest is scratch for other reductions
   void* host_pinned = nullptr;
-  // solver graphs (index 0: mixed FP32 iteration, 1: FP64) and their capture stream
+  // solver graphs and their capture stream
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cap_stream2 = nullptr;          // body of solver loops inside a trajectory capture
-  unsigned long long* counters = nullptr;      // device: iterations, reliable updates, loop trips, trajectory number
+  // device counters: [0] iterations, [1] reliable updates, [2] trips of solver
+  // loops, [3] trajectory number, [4] trips of the heatbath solver loop of an
+  // RHMC trajectory
+  unsigned long long* counters = nullptr;
+  int trip_slot = 2;                           // counter of the trips of an inline solver loop
   unsigned long long inline_body_launches = 0; // kernels per trip of an inline solver loop
-  wz::SolverGraph solver_graph[2];
+  wz::SolverGraph solver_graph[4];             // [mixed, FP64] x [plain, preconditioned]
   wz::TrajGraph traj_graph;
 };
 
 #define WZ_PINNED_BYTES (256 * 1024)
+#define WZ_NCOUNTERS 8
 #define WZ_PINNED_SCRATCH_OFFSET (128 * 1024)
 
 namespace wz {

@@ -20,6 +20,18 @@
 
 namespace wz {
 
+// r(x) = a0 + sum_i alpha_i / (x + beta_i) applied to systems laid out
+// [member][pole][rhs] (inner = rhs per member): the weights of a rational
+// action's force and the combination a0 in + sum_i alpha_i X_i (Eq. jkjk).
+// d = 0 marks the single-pole action (weight 1, no combination).
+struct PoleSum {
+  int d = 0;
+  int inner = 1;
+  double a0 = 0.0;
+  double alpha[WZ_SHIFT_MAX] = {0.0};
+  __host__ __device__ double weight(int q) const { return d ? alpha[(q / inner) % d] : 1.0; }
+};
+
 template <typename R> struct ForceArgs {
   const cplx<R>* A;       // momentum intermediate (input of the inverse passes)
   cplx<R>* A_out;         // xy_boson_fwd output
@@ -38,6 +50,7 @@ template <typename R> struct ForceArgs {
   int TZ;
   int nblk;
   long V;
+  PoleSum pw;             // xy_force: per-system weight alpha_i of the rational action
 };
 
 template <typename R>
@@ -75,6 +88,7 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_force(ForceArgs<double
   const int member = k / a.rpm;
   const SiteCoef<R> kc = a.kArr[member];
   const cplx<R> cg{kc.cg_re, kc.cg_im};
+  const R wk = a.pw.weight(k);
   // chirality weight: spins 2,3 (P_+) carry c g, spins 0,1 (P_-) carry c g^*
   const cplx<R> wgt = s >= 2 ? cg : conj(cg);
   const R sgn = s >= 2 ? R(1) : R(-1);
@@ -89,8 +103,8 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS) xy_force(ForceArgs<double
       const cplx<R> z = v[y] + site_coef<R, false, true>(kc, f, s) * x;  // Z = M X
       const cplx<R> zx = conj(z) * x;
       const cplx<R> t = wgt * zx;
-      dr = -R(2) * t.x;        // -2 Re[w Z^* X]
-      di = R(2) * sgn * t.y;   // -2 Re[+-i w Z^* X] = +-2 Im[w Z^* X]
+      dr = -R(2) * wk * t.x;        // -2 Re[w Z^* X]
+      di = R(2) * wk * sgn * t.y;   // -2 Re[+-i w Z^* X] = +-2 Im[w Z^* X]
     }
     dr = quad_sum(dr);
     di = quad_sum(di);
@@ -248,6 +262,22 @@ static __global__ void draw_sources(cplx<double>* R, int npf, long V, int nm, co
     const cplx<double> z =
         gauss_pair(member_draw(seed, mid[member], (unsigned)site, (unsigned)(4 * k + s), STREAM_PSEUDOFERMION, traj));
     R[i] = cplx<double>{sc * z.x, sc * z.y};
+  }
+}
+
+// out[m][j] = a0 in[m][j] + sum_i alpha_i X[m][i][j] (n complex values per
+// field; ps.inner fields per member).  Grid (nb, members * inner).
+static __global__ void pole_combine(const cplx<double>* in, const cplx<double>* X, cplx<double>* out, long n,
+                                    PoleSum ps) {
+  const int q = blockIdx.y;
+  const int member = q / ps.inner, j = q % ps.inner;
+  const cplx<double>* src = in + (long)q * n;
+  const cplx<double>* xs = X + ((long)member * ps.d * ps.inner + j) * n;
+  const long pstride = (long)ps.inner * n;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+    cplx<double> acc = ps.a0 * src[i];
+    for (int p = 0; p < ps.d; ++p) acc = acc + ps.alpha[p] * xs[p * pstride + i];
+    out[(long)q * n + i] = acc;
   }
 }
 

@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--hmc-traj", type=int, default=2, help="timed trajectories per precision")
     ap.add_argument("--no-sweep", action="store_true", help="skip the L = 8, 16, 32 apply sweep")
     ap.add_argument("--batch", action="store_true", help="also time the 64-lattice batched workload")
+    ap.add_argument("--no-rhmc", action="store_true", help="skip the rational heatbath / RHMC timings")
+    ap.add_argument("--rhmc-fp64", action="store_true", help="also time the RHMC trajectory with FP64 solves")
     return ap.parse_args()
 
 
@@ -314,6 +316,65 @@ def main():
         hmc["mixed_speedup"] = hmc["fp64"]["ms_per_traj"] / hmc["mixed"]["ms_per_traj"]
         hlat.close()
 
+    # rational heatbath eta = (M^dag M)^1/8 R of the paper's heatbath table: L^3 x 32,
+    # m = 1, g = 0.1, degree 20, poles beta <= 100 preconditioned by M0^-1; the
+    # interval is the free spectrum widened by 2 on both ends.  Then RHMC
+    # trajectories (r_a ~ x^-1/4, r_h ~ x^1/8, degree 20) on the HMC workload.
+    rhmc = None
+    if not args.no_rhmc:
+        rhmc = {"heatbath": [], "paper_gtx285": {"8^3x32": {"single_s": 0.93, "single_iters": 360, "double_s": 3.5,
+                                                           "double_iters": 700},
+                                                "16^3x32": {"single_s": 4.8, "single_iters": 370, "double_s": 20,
+                                                            "double_iters": 730}}}
+        for L in (8, 16):
+            dims = (32, L, L, L)
+            rl = wz.Lattice(dims, m=1.0, g=0.1, stream=stream.cuda_stream)
+            rl.set_phi(torch.from_numpy(synth.scalar_field(dims, 0.5, 0)).cuda())
+            lo, hi = rl.spectral_bounds()
+            rh = wz.wz_rational_minimax(0.125, 0.5 * lo, 2.0 * hi, 20)
+            R = torch.from_numpy(synth.spinor_rhs(1, dims, 1)).cuda()
+            eta = torch.empty_like(R)
+            row = {"lattice": f"{L}^3x32", "degree": 20, "interval": [0.5 * lo, 2.0 * hi], "approx_err": rh.err}
+            for label, mixed, tol, pc in (("mixed_1e-6_pc", True, 1e-6, True), ("mixed_1e-10_pc", True, 1e-10, True),
+                                          ("fp64_1e-12_pc", False, 1e-12, True), ("mixed_1e-10_nopc", True, 1e-10, False)):
+                rl.rational_apply(rh, R, eta, tol=tol, mixed=mixed, pc=pc)  # warm-up (graphs, tuner)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                st = rl.rational_apply(rh, R, eta, tol=tol, mixed=mixed, pc=pc)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                row[label] = {"seconds": e0.elapsed_time(e1) / 1000.0, "total_iterations": st["total_iterations"],
+                              "max_iterations": st["iterations"], "reliable_updates": st["reliable_updates"]}
+            rhmc["heatbath"].append(row)
+            rl.close()
+        hw = synth.FORCE_16
+        tl = wz.Lattice(hw.dims, m=hw.m, g=hw.g, stream=stream.cuda_stream)
+        lo, hi = tl.spectral_bounds()
+        ra = wz.wz_rational_minimax(-0.25, 0.5 * lo, 2.0 * hi, 20)
+        rh = wz.wz_rational_minimax(0.125, 0.5 * lo, 2.0 * hi, 20)
+        rhmc["trajectory"] = {"workload": f"{hw.name}: 16^4, m={hw.m}, g={hw.g}, 1 pseudofermion, degree 20 "
+                                          f"(action err {ra.err:.2e}, heatbath err {rh.err:.2e}), "
+                                          f"tau={hw.extra['tau']}, {hw.extra['nsteps']} leapfrog steps, CG to 1e-10"}
+        for label, flags in (("mixed", 0),) + ((("fp64", wz.WZ_HMC_FP64_SOLVES),) if args.rhmc_fp64 else ()):
+            tl.set_phi(torch.from_numpy(synth.scalar_field(hw.dims, hw.sigma, 0)).cuda())
+            kw = dict(tau=hw.extra["tau"], nsteps=hw.extra["nsteps"], npf=1, tol=1e-10, seed=2024, flags=flags)
+            tl.rhmc_trajectory(ra, rh, traj_index=0, **kw)  # warm-up (graph capture)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sts = []
+            e0.record(stream)
+            for t in range(args.hmc_traj):
+                sts.append(tl.rhmc_trajectory(ra, rh, traj_index=1 + t, **kw))
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            rhmc["trajectory"][label] = {"ms_per_traj": ms / args.hmc_traj,
+                                         "cg_iterations_per_traj": float(np.mean([x["cg_iterations"] for x in sts])),
+                                         "dH": [round(x["dH"], 5) for x in sts],
+                                         "accept": [x["accept"] for x in sts]}
+        tl.close()
+
     # apply-throughput sweep: (M^dag M) on L^4, FP32 vs FP64 fields, about 1M
     # site-RHS per launch sequence (256 / 16 / 1 right-hand sides at L = 8/16/32)
     sweep = None
@@ -428,7 +489,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
         }))
     lat.close()

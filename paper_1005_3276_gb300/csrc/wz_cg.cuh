@@ -42,9 +42,10 @@
 #pragma once
 #include "../../include/wz.h"
 #include "wz_kernels.cuh"
+#include "wz_tma.cuh"
 
-// blocks per SM the CG passes are compiled for (85 registers a thread at 256
-// threads); measured against 1, 2 and 4 on the 16^4 x 12 RHS solve
+// register budget of the CG passes, in 256-thread blocks per SM (3: 85
+// registers a thread); measured against 1, 2 and 4 on the 16^4 x 12 RHS solve
 #ifndef WZ_XY_MINB
 #define WZ_XY_MINB 3
 #endif
@@ -134,21 +135,98 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Shared memory of xy_cg: the plane workspace (PPC planes with row padding),
+// 33 reduction doubles, two mbarriers and, in the staged FP32 iteration passes,
+// one buffer of PPC planes per staged operand.  Staged (bulk copies issued at
+// block entry, so they overlap the phase-A FFT): P1 r, p and x (x into the
+// workspace, which P1 only needs after phase B); P3 the momentum input A (into
+// the workspace) and p; P5 A and C (r, read last, is prefetched into L2: a
+// second buffer would cost P5 a block per SM).  Extents up to 16 (the buffers of
+// larger planes would cut the blocks per SM below what hides the FFT).
+template <typename R, int L, int MODE> struct CGSmem {
+  using S = XYShape<L>;
+  static constexpr bool STAGE = sizeof(R) == 4 && L <= 16 && (MODE == CG_P1 || MODE == CG_P3 || MODE == CG_P5);
+  static constexpr int NSTAGE = !STAGE ? 0 : (MODE == CG_P3 ? 1 : 2);
+  static constexpr int PLANE_ELEMS = L * L * 4;  // complex values of one plane, contiguous in global memory
+  static constexpr size_t plane_bytes = sizeof(cplx<R>) * PLANE_ELEMS;
+  static constexpr size_t red_off = sizeof(cplx<R>) * S::PLANE * S::PPC;
+  static constexpr size_t bar_off = (red_off + 33 * sizeof(double) + 15) & ~size_t(15);
+  static constexpr size_t stage_off = (bar_off + 2 * sizeof(unsigned long long) + 127) & ~size_t(127);
+  static constexpr size_t total = STAGE ? stage_off + NSTAGE * S::PPC * plane_bytes : red_off + 33 * sizeof(double);
+  static_assert(!STAGE || plane_bytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
+
 template <typename R, typename LO, int L, int MODE, bool PC>
-__global__ void __launch_bounds__(XYShape<L>::THREADS, WZ_XY_MINB)
+__global__ void __launch_bounds__(XYShape<L>::THREADS, (WZ_XY_MINB * 256) / XYShape<L>::THREADS)
 xy_cg(CGArgs<R, LO> a) {
   using S = XYShape<L>;
   using H = XYPhase<R, L>;
+  using SM = CGSmem<R, L, MODE>;
+  constexpr bool STAGE = SM::STAGE;
+  constexpr int PE = SM::PLANE_ELEMS;
   constexpr bool INV = (MODE == CG_P3 || MODE == CG_P5 || MODE == RU_P5);
   constexpr bool FWD = (MODE == CG_P1 || MODE == CG_P3 || MODE == RU_P1);
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
-  double* red = reinterpret_cast<double*>(sm + S::PLANE * S::PPC);  // 33 doubles
+  double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);  // 33 doubles
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + SM::bar_off);
+  cplx<R>* stg = reinterpret_cast<cplx<R>*>(smem_raw + SM::stage_off);  // [NSTAGE][PPC][PE]
 
   const int rhs = blockIdx.y + a.rhs0;
   RhsState* st = a.st + rhs;
   if (!(a.gate_ru ? st->ru : st->run)) return;  // whole block, before any barrier
   const double shift = st->shift;
+
+  // staged operands: one bulk copy per operand for the block's consecutive planes
+  bool stage_x = false, stage_p = false;
+  if constexpr (STAGE) {
+    if constexpr (MODE == CG_P1) {
+      stage_x = st->alpha != 0.0;
+      stage_p = stage_x || st->beta != 0.0;
+    }
+    if (threadIdx.x == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const int nlive = min(S::PPC, a.TZ - (int)blockIdx.x * S::PPC);
+      const unsigned nb = (unsigned)(nlive * SM::plane_bytes);
+      const long off0 = ((long)rhs * a.TZ + (long)blockIdx.x * S::PPC) * PE;
+      if constexpr (MODE == CG_P1) {
+        mbar_arrive_expect_tx(&bars[1], nb * (1u + (stage_p ? 1u : 0u) + (stage_x ? 1u : 0u)));
+        bulk_g2s(stg, a.r + off0, nb, &bars[1]);
+        if (stage_p) bulk_g2s(stg + S::PPC * PE, a.p + off0, nb, &bars[1]);
+        if (stage_x) bulk_g2s(sm, a.x + off0, nb, &bars[1]);
+      } else {
+        mbar_arrive_expect_tx(&bars[0], nb);
+        bulk_g2s(sm, a.A + off0, nb, &bars[0]);
+        if constexpr (MODE == CG_P3) {
+          mbar_arrive_expect_tx(&bars[1], nb);
+          bulk_g2s(stg, a.p + off0, nb, &bars[1]);
+        } else {
+          mbar_arrive_expect_tx(&bars[1], 2 * nb);
+          bulk_g2s(stg, a.Cb + off0, nb, &bars[1]);
+          bulk_g2s(stg + S::PPC * PE, a.r + off0, nb, &bars[1]);
+        }
+      }
+    }
+  }
+  // a staged wait that ran out: mark this right-hand side failed, let the
+  // copies in flight land (bounded) and leave as a whole block
+  auto stage_failed = [&](bool ok) -> bool {
+    if (!__syncthreads_or(!ok)) return false;
+    if (threadIdx.x == 0) {
+      st->status = WZ_ECUDA;
+      st->run = 0;
+      st->ru = 0;
+      st->active = 0;
+    }
+    if (MODE != CG_P1) mbar_wait_bounded(&bars[0], 0);
+    mbar_wait_bounded(&bars[1], 0);
+    return true;
+  };
 
   const int tid = threadIdx.x;
   if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
@@ -177,10 +255,12 @@ xy_cg(CGArgs<R, LO> a) {
     const long pe = plane * (long)(L * L) * 4;
     if constexpr (MODE == CG_P5) {
       if (!PC && shift != 0.0) prefetch_l2(Pp + pe, PB);
-      prefetch_l2(Pc + pe, PB);
-      prefetch_l2(Pr + pe, PB);
+      if constexpr (!STAGE) {
+        prefetch_l2(Pc + pe, PB);
+        prefetch_l2(Pr + pe, PB);
+      }
     } else if constexpr (MODE == CG_P3) {
-      prefetch_l2(Pp + pe, PB);
+      if constexpr (!STAGE) prefetch_l2(Pp + pe, PB);
     } else if constexpr (MODE == RU_P5) {
       prefetch_l2(Pp + pe, PB);
       prefetch_l2(Pc + pe, PB);
@@ -197,9 +277,31 @@ xy_cg(CGArgs<R, LO> a) {
     }
   }
   if (INV) {
-    if (live) H::inv_x(a.A + base, P, w, s, v);
+    if constexpr (STAGE) {
+      // the plane's momentum input sits unpadded at the start of the workspace
+      if (stage_failed(mbar_wait_bounded(&bars[0], 0))) return;
+      if (live) {
+        const cplx<R>* Ain = sm + pl_local * PE;
+#pragma unroll
+        for (int x = 0; x < L; ++x) v[x] = Ain[(x * L + w) * 4 + s];
+      }
+      __syncthreads();
+      if (live) {
+        fft_line<L, +1, R>(v);
+#pragma unroll
+        for (int x = 0; x < L; ++x) P[w * S::RP + x * 4 + s] = v[x];
+      }
+    } else {
+      if (live) H::inv_x(a.A + base, P, w, s, v);
+    }
     __syncthreads();
   }
+  if constexpr (STAGE) {
+    if (stage_failed(mbar_wait_bounded(&bars[1], 0))) return;
+  }
+  const cplx<R>* S0 = stg + pl_local * PE;                // first staged operand of this plane
+  const cplx<R>* S1 = stg + S::PPC * PE + pl_local * PE;  // second
+  const cplx<R>* SX = sm + pl_local * PE;                 // P1: staged x in the workspace
   R alpha = R(0), beta = R(0);
   if constexpr (MODE == CG_P5) alpha = (R)red[32];
   if constexpr (MODE == CG_P1) {
@@ -225,18 +327,19 @@ xy_cg(CGArgs<R, LO> a) {
 #pragma unroll
     for (int y = 0; y < L; ++y) {
       const long e = (site0 + y * L) * 4 + s;
+      const int el = (y * L + x) * 4 + s;  // within the plane (staged copies)
       if constexpr (MODE == CG_P1) {
         // beta == 0 and alpha == 0 (first step): p = r without reading the previous p
-        cplx<R> pv = Pr[e];
+        cplx<R> pv = STAGE ? S0[el] : Pr[e];
         if (beta != R(0) || alpha != R(0)) {
-          const cplx<R> po = Pp[e];
-          if (alpha != R(0)) Px[e] = Px[e] + alpha * po;
+          const cplx<R> po = STAGE ? S1[el] : Pp[e];
+          if (alpha != R(0)) Px[e] = (STAGE ? SX[el] : Px[e]) + alpha * po;
           pv = pv + beta * po;
         }
         Pp[e] = pv;
         v[y] = pv;
       } else if constexpr (MODE == CG_P3) {
-        const cplx<R> pe = Pp[e];
+        const cplx<R> pe = STAGE ? S0[el] : Pp[e];
         const cplx<R> f = a.phi[phib + y * L];
         if constexpr (PC) {
           const cplx<R> u = v[y];  // M0^-1 p
@@ -251,12 +354,13 @@ xy_cg(CGArgs<R, LO> a) {
           part += norm2(v[y]) + sigma * norm2(pe);
         }
       } else if constexpr (MODE == CG_P5 || MODE == RU_P5) {
+        const cplx<R> cv = STAGE ? S0[el] : Pc[e];
         cplx<R> ap;
-        if constexpr (PC) ap = Pc[e] + v[y];
-        else ap = v[y] + site_coef<R, true, true>(kc, a.phi[phib + y * L], s) * Pc[e];
+        if constexpr (PC) ap = cv + v[y];
+        else ap = v[y] + site_coef<R, true, true>(kc, a.phi[phib + y * L], s) * cv;
         if (!PC && sigma != R(0)) ap = ap + sigma * Pp[e];  // p, or x_hi for RU_P5
         if constexpr (MODE == CG_P5) {
-          const cplx<R> rn = Pr[e] - alpha * ap;
+          const cplx<R> rn = (STAGE ? S1[el] : Pr[e]) - alpha * ap;
           Pr[e] = rn;
           part += norm2(rn);
         } else {
@@ -276,8 +380,12 @@ xy_cg(CGArgs<R, LO> a) {
     if (FWD) {
 #pragma unroll
       for (int y = 0; y < L; ++y) v[y] = twf * v[y];
-      H::fwd_y(v, P, w, s);
     }
+  }
+  // P1 staged x in the workspace: every thread is done with it before fwd_y
+  if constexpr (STAGE && MODE == CG_P1) __syncthreads();
+  if constexpr (FWD) {
+    if (live) H::fwd_y(v, P, w, s);
   }
   if constexpr (FWD) {
     __syncthreads();

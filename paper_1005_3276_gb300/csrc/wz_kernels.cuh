@@ -91,12 +91,16 @@ template <typename R> struct XYArgs {
 };
 
 // Threads per plane: 4 * L (one per (line, spin)); PPC planes per block, the
-// largest count with at most 256 threads and whole warps (block reductions
-// shuffle over full warps).
+// largest count with at most WZ_XY_MAX_THREADS threads and whole warps (block
+// reductions shuffle over full warps).
+#ifndef WZ_XY_MAX_THREADS
+#define WZ_XY_MAX_THREADS 128
+#endif
 constexpr int xy_ppc(int tpp) {
-  int best = 1;
-  for (int k = 1; k * tpp <= 256; ++k)
-    if ((k * tpp) % 32 == 0) best = k;
+  int k0 = 1;  // fewest planes that make whole warps
+  while ((k0 * tpp) % 32) ++k0;
+  int best = k0;
+  for (int k = k0; k * tpp <= WZ_XY_MAX_THREADS; k += k0) best = k;
   return best;
 }
 template <int L> struct XYShape {

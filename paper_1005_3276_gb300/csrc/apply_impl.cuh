@@ -39,9 +39,11 @@ template <typename R> static XYArgs<R> xy_args(const wz_ctx* c, int nrhs) {
   return a;
 }
 
+// the column tile of zt_pass<R, nz, nt> (ZTShape::C), from the runtime extents
 template <typename R> static int zt_cols(int nz, int nt) {
   const int n = nz > nt ? nz : nt;
-  return n <= 16 ? ZTTile<R, 16>::C : (n <= 32 ? ZTTile<R, 32>::C : ZTTile<R, 64>::C);
+  const int c = n <= 16 ? ZTTile<R, 16>::C : (n <= 32 ? ZTTile<R, 32>::C : ZTTile<R, 64>::C);
+  return zt_columns(c, nz);
 }
 
 template <typename R> static ZTArgs<R> zt_args(const wz_ctx* c, R sign) {

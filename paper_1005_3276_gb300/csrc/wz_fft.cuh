@@ -20,6 +20,39 @@ template <typename R> struct cplx { R x, y; };
 template <typename R> WZ_HD cplx<R> mk(R a, R b) { return cplx<R>{a, b}; }
 template <typename R> WZ_HD cplx<R> operator+(cplx<R> a, cplx<R> b) { return {a.x + b.x, a.y + b.y}; }
 template <typename R> WZ_HD cplx<R> operator-(cplx<R> a, cplx<R> b) { return {a.x - b.x, a.y - b.y}; }
+// FP32 complex add / subtract as one packed f32x2 instruction on sm_100 and
+// later (the two components are independent lanes; round to nearest as the
+// scalar forms)
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+__device__ __forceinline__ unsigned long long f2_pack(cplx<float> a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ cplx<float> f2_unpack(unsigned long long r) {
+  cplx<float> a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+#endif
+WZ_HD cplx<float> operator+(cplx<float> a, cplx<float> b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  unsigned long long d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+#else
+  return {a.x + b.x, a.y + b.y};
+#endif
+}
+WZ_HD cplx<float> operator-(cplx<float> a, cplx<float> b) {
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(d);
+#else
+  return {a.x - b.x, a.y - b.y};
+#endif
+}
 template <typename R> WZ_HD cplx<R> operator*(cplx<R> a, cplx<R> b) {
   return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
 }

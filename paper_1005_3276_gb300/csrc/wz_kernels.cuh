@@ -273,23 +273,30 @@ template <typename R> struct ZTArgs {
 
 // Columns per block: 256 B contiguous per (z, t) row for short lines, fewer
 // columns for long lines so that a block stays at <= 512 threads.
+#ifndef WZ_ZT_C0
+#define WZ_ZT_C0 4
+#endif
 template <typename R, int NMAX> struct ZTTile {
-  // 4 columns = 128 B (FP32) / 256 B (FP64) contiguous per (z, t) row; at
-  // 16^2 this gives 256-thread blocks, two of which fit an SM
-  static constexpr int C0 = 4;
+  // C0 columns = 8 C0 B (FP32) / 16 C0 B (FP64) contiguous per (z, t) row;
+  // 4 at 16^2 gives 256-thread blocks (measured against 2 on the 16^4 solve)
+  static constexpr int C0 = WZ_ZT_C0;
   static constexpr int C = NMAX <= 16 ? C0 : (NMAX <= 32 ? C0 / 2 : C0 / 4);
 };
 
+// the tile's columns, doubled until the z-phase threads make whole warps
+constexpr int zt_columns(int c, int nz) { return (nz * c * 4) % 32 ? zt_columns(2 * c, nz) : c; }
+
 template <typename R, int NZ, int NT> struct ZTShape {
   static constexpr int NMAX = NZ > NT ? NZ : NT;
-  static constexpr int C = ZTTile<R, NMAX>::C;
+  static constexpr int C = zt_columns(ZTTile<R, NMAX>::C, NZ);
   static constexpr int THREADS = NMAX * C * 4;
   // every warp must lie entirely inside or outside the t-phase (it shuffles)
   static_assert((NZ * C * 4) % 32 == 0, "z extent too small for the column tile");
 };
 
 template <typename R, int NZ, int NT, int MUL>
-__global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS, (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256) ? 4 : 1)
+__global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS,
+                                  (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256) ? 1024 / ZTShape<R, NZ, NT>::THREADS : 1)
 zt_pass(ZTArgs<R> a) {
   constexpr int C = ZTShape<R, NZ, NT>::C;
   extern __shared__ unsigned char smem_raw[];
@@ -341,7 +348,9 @@ zt_pass(ZTArgs<R> a) {
 #pragma unroll
     for (int pt = 0; pt < NT; ++pt) {
       const long pidx = ((long)pt * NZ + pz) * a.XY + col;
-      const R st = a.sinT[pt];
+      // sin p_t, p_t = pi (2 pt + 1) / T: a compile-time entry of the twiddle table
+      static_assert(WZ_TW_N % (2 * NT) == 0, "antiperiodic momenta must lie on the twiddle grid");
+      const R st = Tw<R>::cosk(((2 * pt + 1) * (WZ_TW_N / (2 * NT)) + 3 * WZ_TW_N / 4) % WZ_TW_N);
       // row of  sum_mu s_mu gamma_mu  acting on the opposite-chirality pair (u, w)
       cplx<R> cu, cw;
       if ((s & 1) == 0) {

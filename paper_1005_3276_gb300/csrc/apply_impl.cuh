@@ -67,6 +67,8 @@ template <typename R> static ZTArgs<R> zt_args(const wz_ctx* c, R sign) {
   a.XY = c->X * c->Y;
   const int C = zt_cols<R>(c->Z, c->T);
   a.ntiles = (a.XY + C - 1) / C;
+  a.fail = (int*)(c->counters + WZ_COUNTER_DEVICE_ERROR);  // sticky device error word of the context
+  a.fail_stride = 0;
   return a;
 }
 

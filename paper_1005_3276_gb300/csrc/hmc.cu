@@ -546,6 +546,7 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st, const 
   if (graph)
     count_launch(c->traj_graph.outer_launches + hc[2] * c->traj_graph.body_launches +
                  hc[4] * c->traj_graph.body_launches_h);
+  if (hc[WZ_COUNTER_DEVICE_ERROR]) return set_error(c, WZ_ECUDA, "trajectory: a device-side copy wait ran out");
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int j = 0; st && j < nm; ++j) {
     st[j].H0 = hres[5 * j + 0];

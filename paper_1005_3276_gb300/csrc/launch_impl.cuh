@@ -2,9 +2,45 @@
 // algorithmic bytes for the probe.  Included only by the kern_L*.cu and
 // zt_*.cu translation units, which instantiate them once per extent.
 #pragma once
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
+
 #include "launch.h"
 
 namespace wz {
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool looked = false;
+  if (!looked) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+    looked = true;
+  }
+  return fn;
+}
+
+// Tensor map of a zt-pass field A [rhs][t][z][XY][4] for nrhs right-hand sides:
+// 3D in 8-byte elements, (XY * 4 * U, Z, T * nrhs), box (C * 4 * U, Z, T) = one tile.
+template <typename R, int NZ, int NT>
+static cudaError_t zt_tensor_map(const ZTArgs<R>& a, int nrhs, CUtensorMap* m) {
+  constexpr int U = sizeof(cplx<R>) / 8;
+  constexpr int C = ZTShape<R, NZ, NT>::C;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  const cuuint64_t row = (cuuint64_t)a.XY * 4 * U;  // elements of one (t, z) row
+  cuuint64_t dims[3] = {row, (cuuint64_t)NZ, (cuuint64_t)NT * nrhs};
+  cuuint64_t strides[2] = {row * 8, row * 8 * NZ};  // bytes, dimensions 1 and 2
+  cuuint32_t box[3] = {(cuuint32_t)(C * 4 * U), (cuuint32_t)NZ, (cuuint32_t)NT};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, (void*)a.A, dims, strides, box, estr,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
 
 template <typename R, int L, int MODE>
@@ -55,7 +91,7 @@ template <typename R, int NZ, int NT, int MUL>
 static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   using S = ZTShape<R, NZ, NT>;
   constexpr int C = S::C;
-  const size_t smem = sizeof(cplx<R>) * NZ * NT * C * 4;
+  const size_t smem = ZTSmem<R, NZ, NT>::total;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = set_smem(zt_pass<R, NZ, NT, MUL>, smem);
@@ -64,6 +100,21 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   }
   const long grid = (long)nrhs * a.ntiles;
   if (grid == 0) return cudaSuccess;
+  // the map covers right-hand sides 0 .. rhs0 + nrhs - 1 of A; the last one is reused
+  struct MapCache {
+    const void* A = nullptr;
+    int XY = 0, n = 0;
+    CUtensorMap m;
+  };
+  static thread_local MapCache mc;
+  if (mc.A != (const void*)a.A || mc.XY != a.XY || mc.n != a.rhs0 + nrhs) {
+    cudaError_t e = zt_tensor_map<R, NZ, NT>(a, a.rhs0 + nrhs, &mc.m);
+    if (e != cudaSuccess) return e;
+    mc.A = a.A;
+    mc.XY = a.XY;
+    mc.n = a.rhs0 + nrhs;
+  }
+  const CUtensorMap tm = mc.m;
   // one block reads and writes C columns x NZ x NT sites of 4 spins and reads
   // the momentum tables it needs (1 for Dslash, 2 for M0^-1)
   const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));  // ZT_SCALAR: 2 tables too
@@ -71,7 +122,7 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
     ZTArgs<R> b = a;
     b.blk_count = cnt;
     b.probe_inc = (unsigned long long)bytes;
-    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b);
+    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b, tm);
     return cudaGetLastError();
   });
 }

@@ -139,10 +139,14 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   z1.A = z2.A = A;
   z1.gate = z2.gate = gate_run;
   z1.gate_stride = z2.gate_stride = gate_stride;
+  z1.fail = z2.fail = &st->status;
+  z1.fail_stride = z2.fail_stride = gate_stride;
   ZTArgs<double> y1 = zt_args<double>(c, 1.0), y2 = zt_args<double>(c, -1.0);
   y1.A = y2.A = A64;
   y1.gate = y2.gate = gate_ru;
   y1.gate_stride = y2.gate_stride = gate_stride;
+  y1.fail = y2.fail = &st->status;
+  y1.fail_stride = y2.fail_stride = gate_stride;
   const int mul1 = pc ? ZT_M0INV : ZT_DSLASH, mul2 = pc ? ZT_M0INV_DAG : ZT_DSLASH;
 
   const double delta2 = delta * delta;

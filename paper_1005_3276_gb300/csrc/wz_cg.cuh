@@ -184,6 +184,20 @@ xy_cg(CGArgs<R, LO> a) {
       stage_x = st->alpha != 0.0;
       stage_p = stage_x || st->beta != 0.0;
     }
+    // bulk copies need 16-byte aligned shared and global addresses: checked,
+    // the right-hand side is marked failed and no copy is issued otherwise
+    const bool misaligned = ((smem_u32(sm) | smem_u32(stg)) & 15u) != 0 ||
+                            (((unsigned long long)a.r | (unsigned long long)a.p | (unsigned long long)a.x |
+                              (unsigned long long)a.A | (unsigned long long)a.Cb) & 15ull) != 0;
+    if (__syncthreads_or(misaligned)) {
+      if (threadIdx.x == 0) {
+        st->status = WZ_ECUDA;
+        st->run = 0;
+        st->ru = 0;
+        st->active = 0;
+      }
+      return;
+    }
     if (threadIdx.x == 0) {
       mbar_init(&bars[0], 1);
       mbar_init(&bars[1], 1);

@@ -138,7 +138,7 @@ struct wz_ctx {
   cudaStream_t cap_stream2 = nullptr;          // body of solver loops inside a trajectory capture
   // device counters: [0] iterations, [1] reliable updates, [2] trips of solver
   // loops, [3] trajectory number, [4] trips of the heatbath solver loop of an
-  // RHMC trajectory
+  // RHMC trajectory, [7] sticky device error word (a bounded wait ran out)
   unsigned long long* counters = nullptr;
   int trip_slot = 2;                           // counter of the trips of an inline solver loop
   unsigned long long inline_body_launches = 0; // kernels per trip of an inline solver loop
@@ -148,6 +148,7 @@ struct wz_ctx {
 
 #define WZ_PINNED_BYTES (256 * 1024)
 #define WZ_NCOUNTERS 8
+#define WZ_COUNTER_DEVICE_ERROR 7
 #define WZ_PINNED_SCRATCH_OFFSET (128 * 1024)
 
 namespace wz {

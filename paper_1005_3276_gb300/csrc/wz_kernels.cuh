@@ -24,7 +24,9 @@
 // lanes, so the spin multiply of the zt pass exchanges the opposite-chirality
 // components with warp shuffles.
 #pragma once
+#include "../../include/wz.h"
 #include "wz_fft.cuh"
+#include "wz_tma.cuh"
 
 namespace wz {
 
@@ -266,6 +268,8 @@ template <typename R> struct ZTArgs {
   int X, XY;
   const int* gate;     // optional per-RHS run flag: block returns if gate[rhs * gate_stride] == 0
   int gate_stride;
+  int* fail;           // set to WZ_ECUDA at fail[rhs * fail_stride] if the tile copy did not complete
+  int fail_stride;
   int rhs0;            // first right-hand side of this launch (launches may cover a group of RHS)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
@@ -294,13 +298,28 @@ template <typename R, int NZ, int NT> struct ZTShape {
   static_assert((NZ * C * 4) % 32 == 0, "z extent too small for the column tile");
 };
 
+// One block: C consecutive (p_x, p_y) columns of one right-hand side for all
+// (z, t).  The tile [t][z][c][s] arrives in shared memory with one 3D tensor
+// copy (TMA) and leaves with one tensor store; both FFT phases and the spin
+// multiply work on it in place.  Ragged last tiles: the copy fills columns
+// past X * Y with zeros and the store clips them.  Dynamic shared memory: the
+// tile at the (128-byte aligned) start, its mbarrier right after it; the
+// kernel has no static shared memory, which would move the dynamic start.
+template <typename R, int NZ, int NT> struct ZTSmem {
+  static constexpr unsigned tile = NZ * NT * ZTShape<R, NZ, NT>::C * 4 * sizeof(cplx<R>);
+  static constexpr unsigned bar_off = (tile + 15) & ~15u;
+  static constexpr unsigned total = bar_off + 16;
+};
 template <typename R, int NZ, int NT, int MUL>
 __global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS,
                                   (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256) ? 1024 / ZTShape<R, NZ, NT>::THREADS : 1)
-zt_pass(ZTArgs<R> a) {
+zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA) {
   constexpr int C = ZTShape<R, NZ, NT>::C;
+  constexpr int U = sizeof(cplx<R>) / 8;  // 8-byte tensor elements per complex value
+  constexpr unsigned TILE_BYTES = ZTSmem<R, NZ, NT>::tile;
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);  // [t][z][c][s]
+  unsigned long long& bar = *reinterpret_cast<unsigned long long*>(smem_raw + ZTSmem<R, NZ, NT>::bar_off);
 
   const int tid = threadIdx.x;
   const int s = tid & 3;
@@ -309,14 +328,30 @@ zt_pass(ZTArgs<R> a) {
   const int rhs = blockIdx.x / a.ntiles + a.rhs0;
   if (a.gate && !a.gate[(long)rhs * a.gate_stride]) return;  // whole block, before any barrier
   if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
-  const int col_raw = (blockIdx.x % a.ntiles) * C + c;  // (p_x, p_y) column = p_x * Y + p_y
-  // the last tile may be ragged (X * Y not a multiple of C): lanes past the
-  // end keep computing on zeros so that every warp stays whole for the
-  // shuffles, but never touch memory
-  const bool colok = col_raw < a.XY;
-  const int col = colok ? col_raw : 0;
-  const long ZXY = (long)NZ * a.XY;
-  cplx<R>* A = a.A + ((long)rhs * NT * ZXY + col) * 4 + s;
+  const int tile = blockIdx.x % a.ntiles;
+  const int col_raw = tile * C + c;  // (p_x, p_y) column = p_x * Y + p_y
+  const int col = col_raw < a.XY ? col_raw : 0;  // table lookups of lanes past the ragged end
+
+  // tensor copies need a 128-byte aligned shared-memory tile: checked, the
+  // block records the failure and leaves without any copy if it is not
+  if (__syncthreads_or((smem_u32(sm) & 127u) != 0)) {
+    if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ECUDA;
+    return;
+  }
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar, TILE_BYTES);
+    tma_load_3d(sm, &tmA, tile * C * 4 * U, 0, rhs * NT, &bar);
+  }
+  if (__syncthreads_or(!mbar_wait_bounded(&bar, 0))) {
+    if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ECUDA;
+    mbar_wait_bounded(&bar, 0);
+    return;
+  }
 
   cplx<R> v[NT > NZ ? NT : NZ];
 
@@ -325,7 +360,7 @@ zt_pass(ZTArgs<R> a) {
     const int t = q;
     // (the antiperiodic twist of the fermion is applied by the xy passes)
 #pragma unroll
-    for (int z = 0; z < NZ; ++z) v[z] = colok ? A[((long)t * ZXY + (long)z * a.XY) * 4] : cplx<R>{R(0), R(0)};
+    for (int z = 0; z < NZ; ++z) v[z] = sm[((t * NZ + z) * C + c) * 4 + s];
     fft_ptr<NZ, -1, R>(v);
 #pragma unroll
     for (int z = 0; z < NZ; ++z) sm[((t * NZ + z) * C + c) * 4 + s] = v[z];
@@ -387,16 +422,20 @@ zt_pass(ZTArgs<R> a) {
   }
   __syncthreads();
 
-  // ---------------- z-phase (inverse) and untwist exp(+i pi t / T)
+  // ---------------- z-phase (inverse), back into the tile, one tensor store
   if (q < NT) {
     const int t = q;
 #pragma unroll
     for (int z = 0; z < NZ; ++z) v[z] = sm[((t * NZ + z) * C + c) * 4 + s];
     fft_ptr<NZ, +1, R>(v);
-    if (colok) {
 #pragma unroll
-      for (int z = 0; z < NZ; ++z) A[((long)t * ZXY + (long)z * a.XY) * 4] = v[z];
-    }
+    for (int z = 0; z < NZ; ++z) sm[((t * NZ + z) * C + c) * 4 + s] = v[z];
+  }
+  fence_proxy_async_smem();
+  __syncthreads();
+  if (tid == 0) {
+    tma_store_3d(&tmA, tile * C * 4 * U, 0, rhs * NT, sm);
+    bulk_store_commit_and_wait_read();
   }
 }
 

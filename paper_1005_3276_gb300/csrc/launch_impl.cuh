@@ -42,6 +42,23 @@ static cudaError_t zt_tensor_map(const ZTArgs<R>& a, int nrhs, CUtensorMap* m) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
+// Tensor map of a momentum table [p_t][p_z][column] (R), box (C, Z, T) = one tile's slice.
+template <typename R, int NZ, int NT>
+static cudaError_t zt_table_map(const R* tab, int XY, CUtensorMap* m) {
+  constexpr int C = ZTShape<R, NZ, NT>::C;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return cudaErrorNotSupported;
+  cuuint64_t dims[3] = {(cuuint64_t)XY, (cuuint64_t)NZ, (cuuint64_t)NT};
+  cuuint64_t strides[2] = {(cuuint64_t)XY * sizeof(R), (cuuint64_t)XY * NZ * sizeof(R)};
+  cuuint32_t box[3] = {(cuuint32_t)C, (cuuint32_t)NZ, (cuuint32_t)NT};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = enc(m, sizeof(R) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                         (void*)tab, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 
 template <typename R, int L, int MODE>
 static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
@@ -91,7 +108,8 @@ template <typename R, int NZ, int NT, int MUL>
 static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   using S = ZTShape<R, NZ, NT>;
   constexpr int C = S::C;
-  const size_t smem = ZTSmem<R, NZ, NT>::total;
+  using ZS = ZTSmem<R, NZ, NT, MUL>;
+  const size_t smem = ZS::total;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = set_smem(zt_pass<R, NZ, NT, MUL>, smem);
@@ -101,20 +119,33 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   const long grid = (long)nrhs * a.ntiles;
   if (grid == 0) return cudaSuccess;
   // the map covers right-hand sides 0 .. rhs0 + nrhs - 1 of A; the last one is reused
+  const R* t0 = MUL == ZT_DSLASH ? a.hV : (MUL == ZT_SCALAR ? a.d2sV : a.hdV);
+  const R* t1 = MUL == ZT_DSLASH ? nullptr : (MUL == ZT_SCALAR ? a.ksV : a.dV);
   struct MapCache {
     const void* A = nullptr;
+    const void* t0 = nullptr;
+    const void* t1 = nullptr;
     int XY = 0, n = 0;
-    CUtensorMap m;
+    CUtensorMap m, m0, m1;
   };
   static thread_local MapCache mc;
-  if (mc.A != (const void*)a.A || mc.XY != a.XY || mc.n != a.rhs0 + nrhs) {
+  if (mc.A != (const void*)a.A || mc.XY != a.XY || mc.n != a.rhs0 + nrhs || mc.t0 != t0 || mc.t1 != t1) {
     cudaError_t e = zt_tensor_map<R, NZ, NT>(a, a.rhs0 + nrhs, &mc.m);
-    if (e != cudaSuccess) return e;
+    if (e == cudaSuccess && ZS::NTAB >= 1) e = zt_table_map<R, NZ, NT>(t0, a.XY, &mc.m0);
+    if (e == cudaSuccess && ZS::NTAB >= 2) e = zt_table_map<R, NZ, NT>(t1, a.XY, &mc.m1);
+    if (e != cudaSuccess) {
+      mc.A = nullptr;
+      return e;
+    }
+    if (ZS::NTAB < 1) mc.m0 = mc.m;  // unused parameters
+    if (ZS::NTAB < 2) mc.m1 = mc.m;
     mc.A = a.A;
+    mc.t0 = t0;
+    mc.t1 = t1;
     mc.XY = a.XY;
     mc.n = a.rhs0 + nrhs;
   }
-  const CUtensorMap tm = mc.m;
+  const CUtensorMap tm = mc.m, tm0 = mc.m0, tm1 = mc.m1;
   // one block reads and writes C columns x NZ x NT sites of 4 spins and reads
   // the momentum tables it needs (1 for Dslash, 2 for M0^-1)
   const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));  // ZT_SCALAR: 2 tables too
@@ -122,7 +153,7 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
     ZTArgs<R> b = a;
     b.blk_count = cnt;
     b.probe_inc = (unsigned long long)bytes;
-    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b, tm);
+    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b, tm, tm0, tm1);
     return cudaGetLastError();
   });
 }

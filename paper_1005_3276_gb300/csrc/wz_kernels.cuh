@@ -302,24 +302,38 @@ template <typename R, int NZ, int NT> struct ZTShape {
 // (z, t).  The tile [t][z][c][s] arrives in shared memory with one 3D tensor
 // copy (TMA) and leaves with one tensor store; both FFT phases and the spin
 // multiply work on it in place.  Ragged last tiles: the copy fills columns
-// past X * Y with zeros and the store clips them.  Dynamic shared memory: the
-// tile at the (128-byte aligned) start, its mbarrier right after it; the
-// kernel has no static shared memory, which would move the dynamic start.
-template <typename R, int NZ, int NT> struct ZTSmem {
-  static constexpr unsigned tile = NZ * NT * ZTShape<R, NZ, NT>::C * 4 * sizeof(cplx<R>);
-  static constexpr unsigned bar_off = (tile + 15) & ~15u;
+// past X * Y with zeros and the store clips them.  The momentum tables of the
+// multiply ([p_t][p_z][column], one or two of them) come the same way, as a
+// (C, NZ, NT) box, in FP32 where C columns make a whole 16-byte row (else they
+// are read from global memory).  Dynamic shared memory: the tile at the (128-byte
+// aligned) start, the table boxes, the mbarrier; the kernel has no static
+// shared memory, which would move the dynamic start.
+template <typename R, int NZ, int NT, int MUL> struct ZTSmem {
+  static constexpr int C = ZTShape<R, NZ, NT>::C;
+  static constexpr unsigned tile = NZ * NT * C * 4 * sizeof(cplx<R>);
+  // FP32 only: the FP64 passes are arithmetic-bound and keep their blocks per SM
+  static constexpr bool STAGE_TAB = sizeof(R) == 4 && (C * sizeof(R)) % 16 == 0;
+  static constexpr int NTAB = STAGE_TAB ? (MUL == ZT_DSLASH ? 1 : 2) : 0;
+  static constexpr unsigned tab = NZ * NT * C * sizeof(R);
+  static constexpr unsigned tab_stride = (tab + 127) & ~127u;  // every box starts 128-byte aligned
+  static constexpr unsigned tab_off = (tile + 127) & ~127u;
+  static constexpr unsigned bar_off = (tab_off + NTAB * tab_stride + 15) & ~15u;
   static constexpr unsigned total = bar_off + 16;
 };
 template <typename R, int NZ, int NT, int MUL>
 __global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS,
                                   (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256) ? 1024 / ZTShape<R, NZ, NT>::THREADS : 1)
-zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA) {
+zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmT0,
+        const __grid_constant__ CUtensorMap tmT1) {
+  using ZS = ZTSmem<R, NZ, NT, MUL>;
   constexpr int C = ZTShape<R, NZ, NT>::C;
   constexpr int U = sizeof(cplx<R>) / 8;  // 8-byte tensor elements per complex value
-  constexpr unsigned TILE_BYTES = ZTSmem<R, NZ, NT>::tile;
+  constexpr unsigned TILE_BYTES = ZS::tile;
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);  // [t][z][c][s]
-  unsigned long long& bar = *reinterpret_cast<unsigned long long*>(smem_raw + ZTSmem<R, NZ, NT>::bar_off);
+  const R* tab0 = reinterpret_cast<const R*>(smem_raw + ZS::tab_off);  // [pt][pz][c]
+  const R* tab1 = reinterpret_cast<const R*>(smem_raw + ZS::tab_off + ZS::tab_stride);
+  unsigned long long& bar = *reinterpret_cast<unsigned long long*>(smem_raw + ZS::bar_off);
 
   const int tid = threadIdx.x;
   const int s = tid & 3;
@@ -344,8 +358,10 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA) {
   }
   __syncthreads();
   if (tid == 0) {
-    mbar_arrive_expect_tx(&bar, TILE_BYTES);
+    mbar_arrive_expect_tx(&bar, TILE_BYTES + ZS::NTAB * ZS::tab);
     tma_load_3d(sm, &tmA, tile * C * 4 * U, 0, rhs * NT, &bar);
+    if constexpr (ZS::NTAB >= 1) tma_load_3d(smem_raw + ZS::tab_off, &tmT0, tile * C, 0, 0, &bar);
+    if constexpr (ZS::NTAB >= 2) tma_load_3d(smem_raw + ZS::tab_off + ZS::tab_stride, &tmT1, tile * C, 0, 0, &bar);
   }
   if (__syncthreads_or(!mbar_wait_bounded(&bar, 0))) {
     if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ECUDA;
@@ -383,6 +399,7 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA) {
 #pragma unroll
     for (int pt = 0; pt < NT; ++pt) {
       const long pidx = ((long)pt * NZ + pz) * a.XY + col;
+      const int tix = (pt * NZ + pz) * C + c;  // staged tables
       // sin p_t, p_t = pi (2 pt + 1) / T: a compile-time entry of the twiddle table
       static_assert(WZ_TW_N % (2 * NT) == 0, "antiperiodic momenta must lie on the twiddle grid");
       const R st = Tw<R>::cosk(((2 * pt + 1) * (WZ_TW_N / (2 * NT)) + 3 * WZ_TW_N / 4) % WZ_TW_N);
@@ -402,13 +419,13 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA) {
       ww.y = __shfl_sync(0xffffffffu, v[pt].y, ulane + 1);
       const cplx<R> g = cu * u + cw * ww;  // (gamma . sin p  in)_s
       if constexpr (MUL == ZT_SCALAR) {
-        const R sc = s == 0 ? a.d2sV[pidx] : (s == 1 ? a.ksV[pidx] : R(0));
+        const R sc = s == 0 ? (ZS::NTAB ? tab0[tix] : a.d2sV[pidx]) : (s == 1 ? (ZS::NTAB ? tab1[tix] : a.ksV[pidx]) : R(0));
         v[pt] = sc * v[pt];
       } else if constexpr (MUL == ZT_DSLASH) {
-        const R hh = a.sign * a.hV[pidx];
+        const R hh = a.sign * (ZS::NTAB ? tab0[tix] : a.hV[pidx]);
         v[pt] = hh * mul_i(g);
       } else {
-        const R hd = a.hdV[pidx], dd = a.dV[pidx];
+        const R hd = ZS::NTAB ? tab0[tix] : a.hdV[pidx], dd = ZS::NTAB ? tab1[tix] : a.dV[pidx];
         // mass on the diagonal: M0^-1 has m^* on P_+ and m on P_-; the dagger swaps
         const bool mconj = (MUL == ZT_M0INV) ? (s >= 2) : (s < 2);
         const cplx<R> mm{a.m_re, mconj ? -a.m_im : a.m_im};

@@ -174,7 +174,7 @@ cudaError_t launch_zt_p(int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) 
 template <typename R, typename LO, int L, int MODE, bool PC>
 static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
   using S = XYShape<L>;
-  const size_t smem = CGSmem<R, L, MODE>::total;
+  const size_t smem = CGSmem<R, L, MODE, PC>::total;
   static bool attr_done = false;
   if (!attr_done) {
     cudaError_t e = set_smem(xy_cg<R, LO, L, MODE, PC>, smem);

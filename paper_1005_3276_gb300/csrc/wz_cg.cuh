@@ -140,20 +140,25 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // one buffer of PPC planes per staged operand.  Staged (bulk copies issued at
 // block entry, so they overlap the phase-A FFT): P1 r, p and x (x into the
 // workspace, which P1 only needs after phase B); P3 the momentum input A (into
-// the workspace) and p; P5 A and C (r, read last, is prefetched into L2: a
-// second buffer would cost P5 a block per SM).  Extents up to 16 (the buffers of
-// larger planes would cut the blocks per SM below what hides the FFT).
-template <typename R, int L, int MODE> struct CGSmem {
+// the workspace) and p; P5 A, C and r; P3 and the unpreconditioned P5 also the
+// phi planes of the site term.  Extents up to 16 (the buffers of larger planes
+// would cut the blocks per SM below what hides the FFT).
+template <typename R, int L, int MODE, bool PC> struct CGSmem {
   using S = XYShape<L>;
   static constexpr bool STAGE = sizeof(R) == 4 && L <= 16 && (MODE == CG_P1 || MODE == CG_P3 || MODE == CG_P5);
   static constexpr int NSTAGE = !STAGE ? 0 : (MODE == CG_P3 ? 1 : 2);
+  static constexpr bool STAGE_PHI = STAGE && (MODE == CG_P3 || (MODE == CG_P5 && !PC));
   static constexpr int PLANE_ELEMS = L * L * 4;  // complex values of one plane, contiguous in global memory
   static constexpr size_t plane_bytes = sizeof(cplx<R>) * PLANE_ELEMS;
+  static constexpr size_t phi_plane_bytes = sizeof(cplx<R>) * L * L;
   static constexpr size_t red_off = sizeof(cplx<R>) * S::PLANE * S::PPC;
   static constexpr size_t bar_off = (red_off + 33 * sizeof(double) + 15) & ~size_t(15);
   static constexpr size_t stage_off = (bar_off + 2 * sizeof(unsigned long long) + 127) & ~size_t(127);
-  static constexpr size_t total = STAGE ? stage_off + NSTAGE * S::PPC * plane_bytes : red_off + 33 * sizeof(double);
-  static_assert(!STAGE || plane_bytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+  static constexpr size_t phi_off = stage_off + NSTAGE * S::PPC * plane_bytes;
+  static constexpr size_t total = STAGE ? phi_off + (STAGE_PHI ? S::PPC * phi_plane_bytes : 0)
+                                        : red_off + 33 * sizeof(double);
+  static_assert(!STAGE || (plane_bytes % 16 == 0 && phi_plane_bytes % 16 == 0),
+                "bulk copies move multiples of 16 bytes");
 };
 
 template <typename R, typename LO, int L, int MODE, bool PC>
@@ -161,7 +166,7 @@ __global__ void __launch_bounds__(XYShape<L>::THREADS, (WZ_XY_MINB * 256) / XYSh
 xy_cg(CGArgs<R, LO> a) {
   using S = XYShape<L>;
   using H = XYPhase<R, L>;
-  using SM = CGSmem<R, L, MODE>;
+  using SM = CGSmem<R, L, MODE, PC>;
   constexpr bool STAGE = SM::STAGE;
   constexpr int PE = SM::PLANE_ELEMS;
   constexpr bool INV = (MODE == CG_P3 || MODE == CG_P5 || MODE == RU_P5);
@@ -171,6 +176,7 @@ xy_cg(CGArgs<R, LO> a) {
   double* red = reinterpret_cast<double*>(smem_raw + SM::red_off);  // 33 doubles
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + SM::bar_off);
   cplx<R>* stg = reinterpret_cast<cplx<R>*>(smem_raw + SM::stage_off);  // [NSTAGE][PPC][PE]
+  cplx<R>* sphi = reinterpret_cast<cplx<R>*>(smem_raw + SM::phi_off);   // [PPC][L * L]
 
   const int rhs = blockIdx.y + a.rhs0;
   RhsState* st = a.st + rhs;
@@ -186,9 +192,10 @@ xy_cg(CGArgs<R, LO> a) {
     }
     // bulk copies need 16-byte aligned shared and global addresses: checked,
     // the right-hand side is marked failed and no copy is issued otherwise
-    const bool misaligned = ((smem_u32(sm) | smem_u32(stg)) & 15u) != 0 ||
+    const bool misaligned = ((smem_u32(sm) | smem_u32(stg) | smem_u32(sphi)) & 15u) != 0 ||
                             (((unsigned long long)a.r | (unsigned long long)a.p | (unsigned long long)a.x |
-                              (unsigned long long)a.A | (unsigned long long)a.Cb) & 15ull) != 0;
+                              (unsigned long long)a.A | (unsigned long long)a.Cb | (unsigned long long)a.phi) &
+                             15ull) != 0;
     if (__syncthreads_or(misaligned)) {
       if (threadIdx.x == 0) {
         st->status = WZ_ECUDA;
@@ -216,14 +223,18 @@ xy_cg(CGArgs<R, LO> a) {
       } else {
         mbar_arrive_expect_tx(&bars[0], nb);
         bulk_g2s(sm, a.A + off0, nb, &bars[0]);
+        // phi planes of the block's member (the planes are consecutive within it)
+        const unsigned nphi = SM::STAGE_PHI ? (unsigned)(nlive * SM::phi_plane_bytes) : 0u;
+        const long phi0 = ((long)(rhs / a.rpm) * a.TZ + (long)blockIdx.x * S::PPC) * (L * L);
         if constexpr (MODE == CG_P3) {
-          mbar_arrive_expect_tx(&bars[1], nb);
+          mbar_arrive_expect_tx(&bars[1], nb + nphi);
           bulk_g2s(stg, a.p + off0, nb, &bars[1]);
         } else {
-          mbar_arrive_expect_tx(&bars[1], 2 * nb);
+          mbar_arrive_expect_tx(&bars[1], 2 * nb + nphi);
           bulk_g2s(stg, a.Cb + off0, nb, &bars[1]);
           bulk_g2s(stg + S::PPC * PE, a.r + off0, nb, &bars[1]);
         }
+        if constexpr (SM::STAGE_PHI) bulk_g2s(sphi, a.phi + phi0, nphi, &bars[1]);
       }
     }
   }
@@ -354,7 +365,7 @@ xy_cg(CGArgs<R, LO> a) {
         v[y] = pv;
       } else if constexpr (MODE == CG_P3) {
         const cplx<R> pe = STAGE ? S0[el] : Pp[e];
-        const cplx<R> f = a.phi[phib + y * L];
+        const cplx<R> f = SM::STAGE_PHI ? sphi[pl_local * (L * L) + y * L + x] : a.phi[phib + y * L];
         if constexpr (PC) {
           const cplx<R> u = v[y];  // M0^-1 p
           const cplx<R> cv = pe + site_coef<R, false, false>(kc, f, s) * u;
@@ -371,7 +382,8 @@ xy_cg(CGArgs<R, LO> a) {
         const cplx<R> cv = STAGE ? S0[el] : Pc[e];
         cplx<R> ap;
         if constexpr (PC) ap = cv + v[y];
-        else ap = v[y] + site_coef<R, true, true>(kc, a.phi[phib + y * L], s) * cv;
+        else ap = v[y] + site_coef<R, true, true>(
+                      kc, SM::STAGE_PHI ? sphi[pl_local * (L * L) + y * L + x] : a.phi[phib + y * L], s) * cv;
         if (!PC && sigma != R(0)) ap = ap + sigma * Pp[e];  // p, or x_hi for RU_P5
         if constexpr (MODE == CG_P5) {
           const cplx<R> rn = (STAGE ? S1[el] : Pr[e]) - alpha * ap;

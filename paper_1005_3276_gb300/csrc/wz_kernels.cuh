@@ -320,9 +320,14 @@ template <typename R, int NZ, int NT, int MUL> struct ZTSmem {
   static constexpr unsigned bar_off = (tab_off + NTAB * tab_stride + 15) & ~15u;
   static constexpr unsigned total = bar_off + 16;
 };
+#ifndef WZ_ZT_RESIDENT_THREADS
+#define WZ_ZT_RESIDENT_THREADS 1024  // FP32 register budget: threads per SM the zt pass is compiled for (1280 measured: no gain)
+#endif
 template <typename R, int NZ, int NT, int MUL>
 __global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS,
-                                  (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256) ? 1024 / ZTShape<R, NZ, NT>::THREADS : 1)
+                                  (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256)
+                                      ? WZ_ZT_RESIDENT_THREADS / ZTShape<R, NZ, NT>::THREADS
+                                      : 1)
 zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmT0,
         const __grid_constant__ CUtensorMap tmT1) {
   using ZS = ZTSmem<R, NZ, NT, MUL>;

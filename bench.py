@@ -107,6 +107,29 @@ def oracle_applies_per_s(w, seconds):
     return n / dt, n, dt
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "zt_pass_fp32_16x4_12rhs.traffic.txt")
+TRAFFIC_SOURCES = ("wz_kernels.cuh", "wz_fft.cuh", "wz_tma.cuh", "launch_impl.cuh", "twiddles.h")
+
+
+def recorded_traffic(kind, real_bytes):
+    """DRAM bytes per launch of the zt pass from the committed ncu record, or None
+    if the probed kernel is another one or its sources changed since the capture."""
+    if kind != "zt" or real_bytes != 4:
+        return None
+    try:
+        rec = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line and not line.startswith("#"))
+    except OSError:
+        return None
+    import hashlib
+    h = hashlib.sha256()
+    for f in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1005_3276_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != rec.get("source_sha256_16", "").strip():
+        return None
+    return float(rec["traffic_bytes_per_launch"])
+
+
 def cpu_threads():
     """Threads the oracle sample actually kept busy: process CPU time / wall time."""
     return getattr(oracle_applies_per_s, "cores", 1)
@@ -470,7 +493,7 @@ def main():
     roofline = {"bound": "hbm", "kernel": f"{dom} (FP{8 * args.probe_bytes})",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_src,
-                "traffic": None, "launches": probe["launches"],
+                "traffic": recorded_traffic(dom, args.probe_bytes), "launches": probe["launches"],
                 "avg_launch_us": 1000.0 * probe["total_ms"] / max(1, probe["timed_launches"]),
                 "algorithmic_bytes_per_launch": probe["bytes"] / max(1, probe["launches"])}
 

@@ -36,6 +36,7 @@ template <typename R> static XYArgs<R> xy_args(const wz_ctx* c, int nrhs) {
   a.Z = c->Z;
   a.twc = tables<R>(c).twc;
   a.tws = tables<R>(c).tws;
+  a.fail = (int*)(c->counters + WZ_COUNTER_DEVICE_ERROR);  // sticky device error word of the context
   return a;
 }
 

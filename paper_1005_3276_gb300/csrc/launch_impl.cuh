@@ -42,10 +42,11 @@ static cudaError_t zt_tensor_map(const ZTArgs<R>& a, int nrhs, CUtensorMap* m) {
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-// Tensor map of a momentum table [p_t][p_z][column] (R), box (C, Z, T) = one tile's slice.
-template <typename R, int NZ, int NT>
+// Tensor map of a momentum table [p_t][p_z][column] (R), box (CB, Z, T): the
+// slice of one tile (CB >= C columns, see ZTSmem).
+template <typename R, int NZ, int NT, int MUL>
 static cudaError_t zt_table_map(const R* tab, int XY, CUtensorMap* m) {
-  constexpr int C = ZTShape<R, NZ, NT>::C;
+  constexpr int C = ZTSmem<R, NZ, NT, MUL>::CB;
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   if (!enc) return cudaErrorNotSupported;
   cuuint64_t dims[3] = {(cuuint64_t)XY, (cuuint64_t)NZ, (cuuint64_t)NT};
@@ -60,16 +61,29 @@ static cudaError_t zt_table_map(const R* tab, int XY, CUtensorMap* m) {
 }
 
 
-template <typename R, int L, int MODE>
-static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
+template <typename R, int L, int MODE, bool STAGE>
+static cudaError_t launch_xy_s(const XYArgs<R>& a, int grid, double blk_bytes, cudaStream_t st) {
   using S = XYShape<L>;
-  const size_t smem = sizeof(cplx<R>) * S::PLANE * S::PPC;
+  const size_t smem = XYSmem<R, L, MODE, STAGE>::total;
   static bool attr_done = false;  // one attribute call per instantiation and process
   if (!attr_done) {
-    cudaError_t e = set_smem(xy_pass<R, L, MODE>, smem);
+    cudaError_t e = set_smem(xy_pass<R, L, MODE, STAGE>, smem);
     if (e != cudaSuccess) return e;
     attr_done = true;
   }
+  return probed(PK_XY, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
+    XYArgs<R> b = a;
+    b.blk_count = cnt;
+    b.probe_inc = (unsigned long long)blk_bytes;
+    xy_pass<R, L, MODE, STAGE><<<grid, S::THREADS, smem, st>>>(b);
+    return cudaGetLastError();
+  });
+}
+
+template <typename R, int L, int MODE>
+static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
+  using S = XYShape<L>;
+  using XS = XYSmem<R, L, MODE, true>;
   const int grid = (a.nplanes + S::PPC - 1) / S::PPC;
   if (grid == 0) return cudaSuccess;
   // algorithmic bytes of one block: the spinor fields it reads and writes,
@@ -79,13 +93,15 @@ static cudaError_t launch_xy_t(const XYArgs<R>& a, cudaStream_t st) {
   const bool uses_phi = !(MODE == XY_FWD || MODE == XY_INV || MODE == XY_INV_ADD);
   const double site = 4.0 * sizeof(cplx<R>) * fields + (uses_phi ? sizeof(cplx<R>) : 0);
   const double blk_bytes = site * L * L * S::PPC;
-  return probed(PK_XY, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
-    XYArgs<R> b = a;
-    b.blk_count = cnt;
-    b.probe_inc = (unsigned long long)blk_bytes;
-    xy_pass<R, L, MODE><<<grid, S::THREADS, smem, st>>>(b);
-    return cudaGetLastError();
-  });
+  // staged form: FP32, extents up to 32, 16-byte aligned operands (the user's
+  // fields may be views at any offset) and blocks of planes within one RHS
+  auto al = [](const void* p) { return ((unsigned long long)p & 15ull) == 0; };
+  const bool stage = sizeof(R) == 4 && L <= 32 && a.TZ % S::PPC == 0 && (!I::inv || al(a.A_in)) &&
+                     (!XS::USES_PSI || al(a.psi)) && (!XS::USES_PHI || al(a.phi));
+  if constexpr (sizeof(R) == 4 && L <= 32) {
+    if (stage) return launch_xy_s<R, L, MODE, true>(a, grid, blk_bytes, st);
+  }
+  return launch_xy_s<R, L, MODE, false>(a, grid, blk_bytes, st);
 }
 
 template <typename R, int L>
@@ -131,8 +147,8 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   static thread_local MapCache mc;
   if (mc.A != (const void*)a.A || mc.XY != a.XY || mc.n != a.rhs0 + nrhs || mc.t0 != t0 || mc.t1 != t1) {
     cudaError_t e = zt_tensor_map<R, NZ, NT>(a, a.rhs0 + nrhs, &mc.m);
-    if (e == cudaSuccess && ZS::NTAB >= 1) e = zt_table_map<R, NZ, NT>(t0, a.XY, &mc.m0);
-    if (e == cudaSuccess && ZS::NTAB >= 2) e = zt_table_map<R, NZ, NT>(t1, a.XY, &mc.m1);
+    if (e == cudaSuccess && ZS::NTAB >= 1) e = zt_table_map<R, NZ, NT, MUL>(t0, a.XY, &mc.m0);
+    if (e == cudaSuccess && ZS::NTAB >= 2) e = zt_table_map<R, NZ, NT, MUL>(t1, a.XY, &mc.m1);
     if (e != cudaSuccess) {
       mc.A = nullptr;
       return e;

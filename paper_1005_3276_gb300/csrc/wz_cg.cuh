@@ -141,11 +141,11 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
 // block entry, so they overlap the phase-A FFT): P1 r, p and x (x into the
 // workspace, which P1 only needs after phase B); P3 the momentum input A (into
 // the workspace) and p; P5 A, C and r; P3 and the unpreconditioned P5 also the
-// phi planes of the site term.  Extents up to 16 (the buffers of larger planes
-// would cut the blocks per SM below what hides the FFT).
+// phi planes of the site term.  Extents up to 32 (at 32 one plane per block:
+// 98 KB for P1, two blocks per SM).
 template <typename R, int L, int MODE, bool PC> struct CGSmem {
   using S = XYShape<L>;
-  static constexpr bool STAGE = sizeof(R) == 4 && L <= 16 && (MODE == CG_P1 || MODE == CG_P3 || MODE == CG_P5);
+  static constexpr bool STAGE = sizeof(R) == 4 && L <= 32 && (MODE == CG_P1 || MODE == CG_P3 || MODE == CG_P5);
   static constexpr int NSTAGE = !STAGE ? 0 : (MODE == CG_P3 ? 1 : 2);
   static constexpr bool STAGE_PHI = STAGE && (MODE == CG_P3 || (MODE == CG_P5 && !PC));
   static constexpr int PLANE_ELEMS = L * L * 4;  // complex values of one plane, contiguous in global memory

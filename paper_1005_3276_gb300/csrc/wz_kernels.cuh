@@ -88,6 +88,7 @@ template <typename R> struct XYArgs {
   int Z;                 // planes per time slice (plane = t * Z + z)
   const R* twc;          // cos(pi t / T): antiperiodic twist, applied in position space
   const R* tws;          // sin(pi t / T)
+  int* fail;             // set to WZ_ECUDA if a staged copy did not complete (may be null)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
@@ -152,13 +153,39 @@ template <typename R, int L> struct XYPhase {
   }
 };
 
-template <typename R, int L, int MODE>
+// Shared memory of xy_pass: the plane workspace; with STAGE (FP32, extents up
+// to 32, 16-byte aligned operands) also one buffer of PPC planes for psi, the
+// phi planes and an mbarrier.  A_in is staged into the workspace (consumed by
+// phase A before the workspace is rewritten), psi and phi into their buffers,
+// all by bulk copies issued at block entry; psi2 (a shift term) is read directly.
+template <typename R, int L, int MODE, bool STAGE> struct XYSmem {
+  using S = XYShape<L>;
+  using I = XYModeInfo<MODE>;
+  static constexpr bool USES_PSI = MODE != XY_INV;
+  static constexpr bool USES_PHI = !(MODE == XY_FWD || MODE == XY_INV || MODE == XY_INV_ADD);
+  static constexpr int PLANE_ELEMS = L * L * 4;
+  static constexpr size_t plane_bytes = sizeof(cplx<R>) * PLANE_ELEMS;
+  static constexpr size_t phi_plane_bytes = sizeof(cplx<R>) * L * L;
+  static constexpr size_t work = sizeof(cplx<R>) * S::PLANE * S::PPC;
+  static constexpr size_t psi_off = (work + 127) & ~size_t(127);
+  static constexpr size_t phi_off = psi_off + (USES_PSI ? S::PPC * plane_bytes : 0);
+  static constexpr size_t bar_off = (phi_off + (USES_PHI ? S::PPC * phi_plane_bytes : 0) + 15) & ~size_t(15);
+  static constexpr size_t total = STAGE ? bar_off + 16 : work;
+  static_assert(plane_bytes % 16 == 0 && phi_plane_bytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+};
+
+template <typename R, int L, int MODE, bool STAGE>
 __global__ void __launch_bounds__(XYShape<L>::THREADS)
 xy_pass(XYArgs<R> a) {
   using S = XYShape<L>;
   using I = XYModeInfo<MODE>;
+  using XS = XYSmem<R, L, MODE, STAGE>;
+  constexpr int PE = XS::PLANE_ELEMS;
   extern __shared__ unsigned char smem_raw[];
   cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);
+  const cplx<R>* spsi = reinterpret_cast<const cplx<R>*>(smem_raw + XS::psi_off);  // [PPC][PE]
+  const cplx<R>* sphi = reinterpret_cast<const cplx<R>*>(smem_raw + XS::phi_off);  // [PPC][L * L]
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smem_raw + XS::bar_off);
 
   const int tid = threadIdx.x;
   const int pl_local = tid / S::TPP;
@@ -170,11 +197,53 @@ xy_pass(XYArgs<R> a) {
   const long base = plane * (long)(L * L) * 4;  // complex offset of the plane
   if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
 
+  if constexpr (STAGE) {
+    // the host launches this form only for 16-byte aligned operands and
+    // right-hand sides of whole blocks of planes (TZ % PPC == 0)
+    if (tid == 0) {
+      mbar_init(bar, 1);
+      mbar_fence_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const long p0 = (long)blockIdx.x * S::PPC;
+      const long nlive = (a.nplanes - p0) < S::PPC ? (a.nplanes - p0) : S::PPC;
+      const unsigned nb = (unsigned)(nlive * XS::plane_bytes);
+      const unsigned nphi = XS::USES_PHI ? (unsigned)(nlive * XS::phi_plane_bytes) : 0u;
+      mbar_arrive_expect_tx(bar, (I::inv ? nb : 0u) + (XS::USES_PSI ? nb : 0u) + nphi);
+      if constexpr (I::inv) bulk_g2s(sm, a.A_in + p0 * PE, nb, bar);
+      if constexpr (XS::USES_PSI) bulk_g2s(smem_raw + XS::psi_off, a.psi + p0 * PE, nb, bar);
+      if constexpr (XS::USES_PHI) {
+        const long member = (p0 / a.TZ) / a.rpm;
+        bulk_g2s(smem_raw + XS::phi_off, a.phi + (member * a.TZ + p0 % a.TZ) * (L * L), nphi, bar);
+      }
+    }
+    if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
+      if (tid == 0 && a.fail) *a.fail = WZ_ECUDA;
+      mbar_wait_bounded(bar, 0);
+      return;
+    }
+  }
+
   cplx<R> v[L];
 
   // ---------------- phase A: inverse FFT along x of the momentum input
   if (I::inv) {
-    if (live) XYPhase<R, L>::inv_x(a.A_in + base, P, w, s, v);
+    if constexpr (STAGE) {
+      if (live) {
+        const cplx<R>* Ain = sm + pl_local * PE;
+#pragma unroll
+        for (int x = 0; x < L; ++x) v[x] = Ain[(x * L + w) * 4 + s];
+      }
+      __syncthreads();
+      if (live) {
+        fft_line<L, +1, R>(v);
+#pragma unroll
+        for (int x = 0; x < L; ++x) P[w * S::RP + x * 4 + s] = v[x];
+      }
+    } else {
+      if (live) XYPhase<R, L>::inv_x(a.A_in + base, P, w, s, v);
+    }
     __syncthreads();
   }
 
@@ -200,26 +269,30 @@ xy_pass(XYArgs<R> a) {
 #pragma unroll
     for (int y = 0; y < L; ++y) {
       const long e = (site0 + y * L) * 4 + s;
+      const int el = pl_local * PE + (y * L + x) * 4 + s;  // staged copies
+      cplx<R> ps{R(0), R(0)}, f{R(0), R(0)};
+      if constexpr (XS::USES_PSI) ps = STAGE ? spsi[el] : a.psi[e];
+      if constexpr (XS::USES_PHI) f = STAGE ? sphi[pl_local * (L * L) + y * L + x] : a.phi[phib + y * L];
       if constexpr (MODE == XY_FWD) {
-        v[y] = a.psi[e];
+        v[y] = ps;
       } else if constexpr (MODE == XY_FWD_YINTDAG) {
-        v[y] = site_coef<R, true, false>(kc, a.phi[phib + y * L], s) * a.psi[e];
+        v[y] = site_coef<R, true, false>(kc, f, s) * ps;
       } else if constexpr (MODE == XY_INV_Y || MODE == XY_INV_Y_FWD) {
-        v[y] = v[y] + site_coef<R, false, true>(kc, a.phi[phib + y * L], s) * a.psi[e];
+        v[y] = v[y] + site_coef<R, false, true>(kc, f, s) * ps;
       } else if constexpr (MODE == XY_INV_YDAG) {
-        v[y] = v[y] + site_coef<R, true, true>(kc, a.phi[phib + y * L], s) * a.psi[e];
+        v[y] = v[y] + site_coef<R, true, true>(kc, f, s) * ps;
         if (a.psi2) v[y] = v[y] + a.shift * a.psi2[e];
       } else if constexpr (MODE == XY_INV_PC || MODE == XY_INV_PC_FWD) {
-        v[y] = a.psi[e] + site_coef<R, false, false>(kc, a.phi[phib + y * L], s) * v[y];
+        v[y] = ps + site_coef<R, false, false>(kc, f, s) * v[y];
       } else if constexpr (MODE == XY_INV_ADD) {
-        v[y] = a.psi[e] + v[y];
+        v[y] = ps + v[y];
         if (a.psi2) v[y] = v[y] + a.shift * a.psi2[e];
       }
       if constexpr (MODE != XY_FWD && MODE != XY_FWD_YINTDAG) {
         if (a.v_out) a.v_out[e] = v[y];
       }
       if constexpr (MODE == XY_INV_PC_FWD) {
-        v[y] = site_coef<R, true, false>(kc, a.phi[phib + y * L], s) * v[y];
+        v[y] = site_coef<R, true, false>(kc, f, s) * v[y];
       }
     }
     if (I::fwd) {
@@ -230,7 +303,8 @@ xy_pass(XYArgs<R> a) {
   }
   if (!I::fwd) return;
   // phase B of thread (x, s) rewrites exactly the smem cells it read, so no
-  // barrier is needed between its reads and these writes
+  // barrier is needed between its reads and these writes (the staged A_in of
+  // an inverse-forward mode was consumed before the barrier of phase A)
   if (live) {
 #pragma unroll
     for (int y = 0; y < L; ++y) P[y * S::RP + w * 4 + s] = v[y];
@@ -303,18 +377,20 @@ template <typename R, int NZ, int NT> struct ZTShape {
 // copy (TMA) and leaves with one tensor store; both FFT phases and the spin
 // multiply work on it in place.  Ragged last tiles: the copy fills columns
 // past X * Y with zeros and the store clips them.  The momentum tables of the
-// multiply ([p_t][p_z][column], one or two of them) come the same way, as a
-// (C, NZ, NT) box, in FP32 where C columns make a whole 16-byte row (else they
-// are read from global memory).  Dynamic shared memory: the tile at the (128-byte
+// multiply ([p_t][p_z][column], one or two of them) come the same way in FP32,
+// as a (CB, NZ, NT) box of CB >= C columns starting at a multiple of CB, CB
+// columns making at least one 16-byte row.  Dynamic shared memory: the tile at the (128-byte
 // aligned) start, the table boxes, the mbarrier; the kernel has no static
 // shared memory, which would move the dynamic start.
 template <typename R, int NZ, int NT, int MUL> struct ZTSmem {
   static constexpr int C = ZTShape<R, NZ, NT>::C;
   static constexpr unsigned tile = NZ * NT * C * 4 * sizeof(cplx<R>);
   // FP32 only: the FP64 passes are arithmetic-bound and keep their blocks per SM
-  static constexpr bool STAGE_TAB = sizeof(R) == 4 && (C * sizeof(R)) % 16 == 0;
+  static constexpr bool STAGE_TAB = sizeof(R) == 4;
+  static constexpr int CB = (int)(C * sizeof(R)) >= 16 ? C : (int)(16 / sizeof(R));  // box columns
+  static_assert(CB % C == 0, "a tile's columns must fall inside one table box");
   static constexpr int NTAB = STAGE_TAB ? (MUL == ZT_DSLASH ? 1 : 2) : 0;
-  static constexpr unsigned tab = NZ * NT * C * sizeof(R);
+  static constexpr unsigned tab = NZ * NT * CB * sizeof(R);
   static constexpr unsigned tab_stride = (tab + 127) & ~127u;  // every box starts 128-byte aligned
   static constexpr unsigned tab_off = (tile + 127) & ~127u;
   static constexpr unsigned bar_off = (tab_off + NTAB * tab_stride + 15) & ~15u;
@@ -365,8 +441,9 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
   if (tid == 0) {
     mbar_arrive_expect_tx(&bar, TILE_BYTES + ZS::NTAB * ZS::tab);
     tma_load_3d(sm, &tmA, tile * C * 4 * U, 0, rhs * NT, &bar);
-    if constexpr (ZS::NTAB >= 1) tma_load_3d(smem_raw + ZS::tab_off, &tmT0, tile * C, 0, 0, &bar);
-    if constexpr (ZS::NTAB >= 2) tma_load_3d(smem_raw + ZS::tab_off + ZS::tab_stride, &tmT1, tile * C, 0, 0, &bar);
+    const int tx0 = (tile * C / ZS::CB) * ZS::CB;  // table box start (multiple of CB columns)
+    if constexpr (ZS::NTAB >= 1) tma_load_3d(smem_raw + ZS::tab_off, &tmT0, tx0, 0, 0, &bar);
+    if constexpr (ZS::NTAB >= 2) tma_load_3d(smem_raw + ZS::tab_off + ZS::tab_stride, &tmT1, tx0, 0, 0, &bar);
   }
   if (__syncthreads_or(!mbar_wait_bounded(&bar, 0))) {
     if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ECUDA;
@@ -404,7 +481,7 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
 #pragma unroll
     for (int pt = 0; pt < NT; ++pt) {
       const long pidx = ((long)pt * NZ + pz) * a.XY + col;
-      const int tix = (pt * NZ + pz) * C + c;  // staged tables
+      const int tix = (pt * NZ + pz) * ZS::CB + (tile * C) % ZS::CB + c;  // staged tables
       // sin p_t, p_t = pi (2 pt + 1) / T: a compile-time entry of the twiddle table
       static_assert(WZ_TW_N % (2 * NT) == 0, "antiperiodic momenta must lie on the twiddle grid");
       const R st = Tw<R>::cosk(((2 * pt + 1) * (WZ_TW_N / (2 * NT)) + 3 * WZ_TW_N / 4) % WZ_TW_N);

@@ -360,6 +360,9 @@ int create_ctx(const wz_params* ps, int nm, void* stream, wz_ctx** out) {
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, WZ_PINNED_BYTES);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->branch_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&c->counters, WZ_NCOUNTERS * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->counters, 0, WZ_NCOUNTERS * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -409,6 +412,9 @@ int wz_destroy(wz_ctx* c) {
   c->traj_graph.release();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+  if (c->branch_stream) cudaStreamDestroy(c->branch_stream);
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->counters) cudaFree(c->counters);
   c->ws_apply.release();
   c->ws_stage.release();

@@ -166,13 +166,99 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   // can stay in L2 between producer and consumer passes.  The group size is
   // chosen per solve shape by timing the candidates (autotune_group below).
   int gsz = nrhs;
+  // With nbranch = 2 the groups are split over two streams (two parallel
+  // branches of the graph), each group with its own scalar and reliable-update
+  // kernels, so that the passes of one group overlap those of the other.
+  int nbranch = 1;
 
   // iteration counters of the chunks (off while the tuner times candidates)
   unsigned long long* cnt = c->counters;
 
+  // K iterations and one reliable-update block of the right-hand sides [r0, r0 + ng)
+  auto issue_group_chunk = [&](int r0, int ng, cudaStream_t q) -> cudaError_t {
+    cudaError_t e2;
+#define WZ_Q(...)                          \
+  do {                                     \
+    e2 = (__VA_ARGS__);                    \
+    if (e2 != cudaSuccess) return e2;      \
+  } while (0)
+    for (int k = 0; k < K; ++k) {
+      CGArgs<RI, RI> a1 = ga;
+      a1.rhs0 = r0;
+      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P1, a1, ng, q));
+      ZTArgs<RI> zz1 = z1;
+      zz1.rhs0 = r0;
+      WZ_Q(launch_zt<RI>(c->Z, c->T, mul1, zz1, ng, q));
+      CGArgs<RI, RI> a3 = ga;
+      a3.rhs0 = r0;
+      a3.part_out = part3;
+      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P3, a3, ng, q));
+      ZTArgs<RI> zz2 = z2;
+      zz2.rhs0 = r0;
+      WZ_Q(launch_zt<RI>(c->Z, c->T, mul2, zz2, ng, q));
+      CGArgs<RI, RI> a5 = ga;
+      a5.rhs0 = r0;
+      a5.part_in = part3;
+      a5.part_out = part5;
+      WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, ng, q));
+      count_launch();
+      cg_scalar_iter<<<ng, 32, 0, q>>>(st + r0, part5 + (long)r0 * nblk, part3 + (long)r0 * nblk, nblk, delta2,
+                                       maxiter, cnt);
+      WZ_Q(cudaGetLastError());
+    }
+    CGArgs<double, RI> u1 = ra;
+    u1.rhs0 = r0;
+    WZ_Q(launch_cg<double, RI>(L, pc, RU_P1, u1, ng, q));
+    ZTArgs<double> w1 = y1;
+    w1.rhs0 = r0;
+    WZ_Q(launch_zt<double>(c->Z, c->T, mul1, w1, ng, q));
+    CGArgs<double, double> u3{};
+    u3.A = A64;
+    u3.Cb = C64;
+    u3.p = xs;
+    u3.phi = c->phi64;
+    u3.kArr = c->k64;
+    u3.rpm = ga.rpm;
+    u3.Z = c->Z;
+    u3.twc = c->t64.twc;
+    u3.tws = c->t64.tws;
+    u3.shifted = ga.shifted;
+    u3.st = st;
+    u3.nblk = nblk;
+    u3.TZ = TZ;
+    u3.gate_ru = 1;
+    u3.rhs0 = r0;
+    WZ_Q(launch_cg<double, double>(L, pc, CG_P3, u3, ng, q));
+    ZTArgs<double> w2 = y2;
+    w2.rhs0 = r0;
+    WZ_Q(launch_zt<double>(c->Z, c->T, mul2, w2, ng, q));
+    CGArgs<double, RI> u5 = ra;
+    u5.rhs0 = r0;
+    u5.part_out = partR;
+    WZ_Q(launch_cg<double, RI>(L, pc, RU_P5, u5, ng, q));
+    count_launch();
+    cg_scalar_ru<<<ng, 32, 0, q>>>(st + r0, partR + (long)r0 * nblk, nblk, maxiter, cnt);
+    WZ_Q(cudaGetLastError());
+#undef WZ_Q
+    return cudaSuccess;
+  };
+
   // one chunk: K iterations and one reliable-update block, all gated on the device
   auto issue_chunk = [&](cudaStream_t q) -> cudaError_t {
     cudaError_t e2;
+    if (nbranch == 2 && gsz < nrhs) {
+      // fork the second stream off q, alternate the groups between them, join
+      cudaStream_t qb = c->branch_stream;
+      if ((e2 = cudaEventRecord(c->ev_fork, q)) != cudaSuccess) return e2;
+      if ((e2 = cudaStreamWaitEvent(qb, c->ev_fork, 0)) != cudaSuccess) return e2;
+      int g = 0;
+      for (int r0 = 0; r0 < nrhs; r0 += gsz, ++g) {
+        const int ng = nrhs - r0 < gsz ? nrhs - r0 : gsz;
+        if ((e2 = issue_group_chunk(r0, ng, (g & 1) ? qb : q)) != cudaSuccess) return e2;
+      }
+      if ((e2 = cudaEventRecord(c->ev_join, qb)) != cudaSuccess) return e2;
+      return cudaStreamWaitEvent(q, c->ev_join, 0);
+    }
 #define WZ_Q(...)                          \
   do {                                     \
     e2 = (__VA_ARGS__);                    \
@@ -233,8 +319,9 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     return cudaSuccess;
   };
 
-  // Autotune the RHS group size once per solve shape: for each candidate,
-  // re-initialise and time two chunks (16 iterations) with CUDA events.
+  // Autotune the RHS group size and the branch count once per solve shape: for
+  // each candidate, re-initialise and time two chunks (16 iterations) with CUDA
+  // events.  The cache holds 4 * gsz + nbranch.
   {
     static std::mutex mu;
     static std::map<std::vector<long>, int> cache;
@@ -247,25 +334,30 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
       if (it != cache.end()) found = it->second;
     }
     const char* forced = getenv("WZ_RHS_GROUP");  // a fixed group size overrides the tuner
+    const char* forced_b = getenv("WZ_RHS_BRANCHES");
     if (forced && atoi(forced) > 0) {
       gsz = atoi(forced) < nrhs ? atoi(forced) : nrhs;
+      nbranch = (forced_b && atoi(forced_b) == 2) ? 2 : 1;
     } else if (found) {
-      gsz = found;
+      gsz = found / 4;
+      nbranch = found % 4;
     } else if (nrhs > 1 && !inline_capture && !g_probe.active) {
-      std::vector<int> cand;
+      std::vector<std::pair<int, int>> cand;
       for (int d : {1, 2, 3, 4, 6, 8})
         if (nrhs / d >= 1) {
           const int g = (nrhs + d - 1) / d;
-          if (std::find(cand.begin(), cand.end(), g) == cand.end()) cand.push_back(g);
+          for (int nb = 1; nb <= (g < nrhs ? 2 : 1); ++nb)
+            if (std::find(cand.begin(), cand.end(), std::make_pair(g, nb)) == cand.end()) cand.emplace_back(g, nb);
         }
       cudaEvent_t e0, e1;
       cnt = nullptr;
       WZ_RUN(cudaEventCreate(&e0));
       WZ_RUN(cudaEventCreate(&e1));
       float best = 1e30f;
-      int bestg = nrhs;
-      for (int g : cand) {
-        gsz = g;
+      int bestg = nrhs, bestb = 1;
+      for (const auto& cb : cand) {
+        gsz = cb.first;
+        nbranch = cb.second;
         WZ_RUN(issue_chunk(s));  // warm-up on whatever state the recursion is in
         WZ_RUN(cudaEventRecord(e0, s));
         WZ_RUN(issue_chunk(s));
@@ -276,7 +368,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
         WZ_RUN(cudaEventElapsedTime(&ms, e0, e1));
         if (ms < best) {
           best = ms;
-          bestg = g;
+          bestg = cb.first;
+          bestb = cb.second;
         }
         // back to the initial state of the solve
         WZ_RUN(cudaMemsetAsync(xs, 0, W.field64, s));
@@ -290,10 +383,14 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
       cudaEventDestroy(e1);
       cnt = c->counters;
       gsz = bestg;
+      nbranch = bestb;
       std::lock_guard<std::mutex> lk(mu);
-      cache[tkey] = gsz;
+      cache[tkey] = 4 * gsz + nbranch;
     }
   }
+
+  // the kernel probe times launches one by one: no concurrent branches then
+  if (g_probe.active) nbranch = 1;
 
   // Graph mode: the whole chunk loop is one CUDA graph whose body sits in a
   // WHILE conditional node; a one-thread kernel at the end of the body keeps
@@ -357,6 +454,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     key.phi64 = c->phi64;
     key.phi32 = c->phi32;
     key.gsz = gsz;
+    key.nbranch = nbranch;
     if (!G.exec || memcmp(&key, &G.key, sizeof(key)) != 0) {
       G.release();
       WZ_CUDA_TRY(c, cudaGraphCreate(&G.graph, 0));

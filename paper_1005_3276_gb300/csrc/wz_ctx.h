@@ -60,7 +60,8 @@ struct SolverGraphKey {
   size_t ws_bytes;
   const void* phi64;
   const void* phi32;
-  int gsz;  // right-hand sides per group
+  int gsz;      // right-hand sides per group
+  int nbranch;  // streams the groups alternate between
 };
 struct SolverGraph {
   SolverGraphKey key{};
@@ -136,6 +137,8 @@ struct wz_ctx {
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cap_stream2 = nullptr;          // body of solver loops inside a trajectory capture
+  cudaStream_t branch_stream = nullptr;        // second branch of a solver chunk (RHS groups)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // device counters: [0] iterations, [1] reliable updates, [2] trips of solver
   // loops, [3] trajectory number, [4] trips of the heatbath solver loop of an
   // RHMC trajectory, [7] sticky device error word (a bounded wait ran out)

@@ -360,9 +360,11 @@ int create_ctx(const wz_params* ps, int nm, void* stream, wz_ctx** out) {
     if (e == cudaSuccess) e = cudaMallocHost(&c->host_pinned, WZ_PINNED_BYTES);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking);
-    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->branch_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    for (int i = 0; i < wz_ctx::kMaxBranches - 1; ++i) {
+      if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->branch_stream[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->ev_join[i], cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&c->counters, WZ_NCOUNTERS * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(c->counters, 0, WZ_NCOUNTERS * sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -412,9 +414,11 @@ int wz_destroy(wz_ctx* c) {
   c->traj_graph.release();
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
-  if (c->branch_stream) cudaStreamDestroy(c->branch_stream);
+  for (int i = 0; i < wz_ctx::kMaxBranches - 1; ++i) {
+    if (c->branch_stream[i]) cudaStreamDestroy(c->branch_stream[i]);
+    if (c->ev_join[i]) cudaEventDestroy(c->ev_join[i]);
+  }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
-  if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->counters) cudaFree(c->counters);
   c->ws_apply.release();
   c->ws_stage.release();

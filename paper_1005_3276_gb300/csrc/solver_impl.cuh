@@ -166,9 +166,9 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   // can stay in L2 between producer and consumer passes.  The group size is
   // chosen per solve shape by timing the candidates (autotune_group below).
   int gsz = nrhs;
-  // With nbranch = 2 the groups are split over two streams (two parallel
+  // With nbranch > 1 the groups alternate between nbranch streams (parallel
   // branches of the graph), each group with its own scalar and reliable-update
-  // kernels, so that the passes of one group overlap those of the other.
+  // kernels, so that the passes of one group overlap those of the others.
   int nbranch = 1;
 
   // iteration counters of the chunks (off while the tuner times candidates)
@@ -246,18 +246,23 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   // one chunk: K iterations and one reliable-update block, all gated on the device
   auto issue_chunk = [&](cudaStream_t q) -> cudaError_t {
     cudaError_t e2;
-    if (nbranch == 2 && gsz < nrhs) {
-      // fork the second stream off q, alternate the groups between them, join
-      cudaStream_t qb = c->branch_stream;
+    if (nbranch > 1 && gsz < nrhs) {
+      // fork the branch streams off q, deal the groups round robin, join
+      const int nb = nbranch;
       if ((e2 = cudaEventRecord(c->ev_fork, q)) != cudaSuccess) return e2;
-      if ((e2 = cudaStreamWaitEvent(qb, c->ev_fork, 0)) != cudaSuccess) return e2;
+      for (int b = 0; b < nb - 1; ++b)
+        if ((e2 = cudaStreamWaitEvent(c->branch_stream[b], c->ev_fork, 0)) != cudaSuccess) return e2;
       int g = 0;
       for (int r0 = 0; r0 < nrhs; r0 += gsz, ++g) {
         const int ng = nrhs - r0 < gsz ? nrhs - r0 : gsz;
-        if ((e2 = issue_group_chunk(r0, ng, (g & 1) ? qb : q)) != cudaSuccess) return e2;
+        const int b = g % nb;
+        if ((e2 = issue_group_chunk(r0, ng, b ? c->branch_stream[b - 1] : q)) != cudaSuccess) return e2;
       }
-      if ((e2 = cudaEventRecord(c->ev_join, qb)) != cudaSuccess) return e2;
-      return cudaStreamWaitEvent(q, c->ev_join, 0);
+      for (int b = 0; b < nb - 1; ++b) {
+        if ((e2 = cudaEventRecord(c->ev_join[b], c->branch_stream[b])) != cudaSuccess) return e2;
+        if ((e2 = cudaStreamWaitEvent(q, c->ev_join[b], 0)) != cudaSuccess) return e2;
+      }
+      return cudaSuccess;
     }
 #define WZ_Q(...)                          \
   do {                                     \
@@ -320,8 +325,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   };
 
   // Autotune the RHS group size and the branch count once per solve shape: for
-  // each candidate, re-initialise and time two chunks (16 iterations) with CUDA
-  // events.  The cache holds 4 * gsz + nbranch.
+  // each candidate, re-initialise and time three chunks (24 iterations) with CUDA
+  // events.  The cache holds 8 * gsz + nbranch.
   {
     static std::mutex mu;
     static std::map<std::vector<long>, int> cache;
@@ -337,16 +342,18 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     const char* forced_b = getenv("WZ_RHS_BRANCHES");
     if (forced && atoi(forced) > 0) {
       gsz = atoi(forced) < nrhs ? atoi(forced) : nrhs;
-      nbranch = (forced_b && atoi(forced_b) == 2) ? 2 : 1;
+      nbranch = forced_b ? atoi(forced_b) : 1;
+      nbranch = nbranch < 1 ? 1 : (nbranch > wz_ctx::kMaxBranches ? wz_ctx::kMaxBranches : nbranch);
     } else if (found) {
-      gsz = found / 4;
-      nbranch = found % 4;
+      gsz = found / 8;
+      nbranch = found % 8;
     } else if (nrhs > 1 && !inline_capture && !g_probe.active) {
       std::vector<std::pair<int, int>> cand;
       for (int d : {1, 2, 3, 4, 6, 8})
         if (nrhs / d >= 1) {
           const int g = (nrhs + d - 1) / d;
-          for (int nb = 1; nb <= (g < nrhs ? 2 : 1); ++nb)
+          const int ngroups = (nrhs + g - 1) / g;
+          for (int nb = 1; nb <= (ngroups < wz_ctx::kMaxBranches ? ngroups : wz_ctx::kMaxBranches); ++nb)
             if (std::find(cand.begin(), cand.end(), std::make_pair(g, nb)) == cand.end()) cand.emplace_back(g, nb);
         }
       cudaEvent_t e0, e1;
@@ -360,8 +367,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
         nbranch = cb.second;
         WZ_RUN(issue_chunk(s));  // warm-up on whatever state the recursion is in
         WZ_RUN(cudaEventRecord(e0, s));
-        WZ_RUN(issue_chunk(s));
-        WZ_RUN(issue_chunk(s));
+        for (int rep = 0; rep < 3; ++rep) WZ_RUN(issue_chunk(s));
         WZ_RUN(cudaEventRecord(e1, s));
         WZ_RUN(cudaEventSynchronize(e1));
         float ms = 0.f;
@@ -385,7 +391,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
       gsz = bestg;
       nbranch = bestb;
       std::lock_guard<std::mutex> lk(mu);
-      cache[tkey] = 4 * gsz + nbranch;
+      cache[tkey] = 8 * gsz + nbranch;
     }
   }
 

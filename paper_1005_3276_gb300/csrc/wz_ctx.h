@@ -137,8 +137,11 @@ struct wz_ctx {
   bool use_graphs = true;
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cap_stream2 = nullptr;          // body of solver loops inside a trajectory capture
-  cudaStream_t branch_stream = nullptr;        // second branch of a solver chunk (RHS groups)
-  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // extra branches of a solver chunk (RHS groups on concurrent streams)
+  static const int kMaxBranches = 4;
+  cudaStream_t branch_stream[kMaxBranches - 1] = {};
+  cudaEvent_t ev_fork = nullptr;
+  cudaEvent_t ev_join[kMaxBranches - 1] = {};
   // device counters: [0] iterations, [1] reliable updates, [2] trips of solver
   // loops, [3] trajectory number, [4] trips of the heatbath solver loop of an
   // RHMC trajectory, [7] sticky device error word (a bounded wait ran out)

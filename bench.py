@@ -497,6 +497,14 @@ def main():
                 "avg_launch_us": 1000.0 * probe["total_ms"] / max(1, probe["timed_launches"]),
                 "algorithmic_bytes_per_launch": probe["bytes"] / max(1, probe["launches"])}
 
+    # the whole CG iteration against the same peak: per M^dag M apply of one RHS
+    # the five passes move 18 FP32 spinor fields (P1 6, zt 2 + 2, P3 4, P5 4)
+    # and phi twice (P3, P5), 18 * 32 + 2 * 8 = 592 B per site (tables not counted)
+    it_bytes = 592.0 * int(np.prod(w.dims))
+    solve_roofline = {"bound": "hbm", "bytes_per_apply": it_bytes, "achieved": value * it_bytes / 1e9,
+                      "peak": peak, "unit": "GB/s", "frac": value * it_bytes / 1e9 / peak,
+                      "note": "mixed solve, reliable updates included in the time, not in the bytes"}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, dt = oracle_applies_per_s(w, args.cpu_seconds)
@@ -512,7 +520,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
         }))
     lat.close()

@@ -347,6 +347,11 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     } else if (found) {
       gsz = found / 8;
       nbranch = found % 8;
+    } else if (inline_capture && nrhs >= 8) {
+      // no timing inside a capture: four groups on four branches (the choice the
+      // tuner makes for 12 right-hand sides at 16^4)
+      gsz = (nrhs + 3) / 4;
+      nbranch = (nrhs + gsz - 1) / gsz;
     } else if (nrhs > 1 && !inline_capture && !g_probe.active) {
       std::vector<std::pair<int, int>> cand;
       for (int d : {1, 2, 3, 4, 6, 8})

@@ -66,7 +66,9 @@ enum wz_op {
   WZ_OP_M0INV_DAG = 5,    /* (M0^-1)^dagger psi                                   */
   WZ_OP_MTILDE = 6,       /* M~ psi = M M0^-1 psi                   (Eq. theprob) */
   WZ_OP_MTILDE_DAG = 7,   /* M~^dagger psi                                        */
-  WZ_OP_MTILDE_DAGM = 8   /* (M~^dagger M~ + shift) psi                           */
+  WZ_OP_MTILDE_DAGM = 8,  /* (M~^dagger M~ + shift) psi                           */
+  WZ_OP_D1 = 9            /* D1 psi: gamma-odd part of the overlap, i gamma.sin p / omega
+                             in momentum space (Sec. 2.2; the D1 of Eqs. uity, nzav) */
 };
 
 /* Lattice and action parameters (Sec. 2.2, Eq. fmat, Eq. acws). */
@@ -264,6 +266,22 @@ int wz_rhmc_trajectory(wz_ctx* ctx, const wz_hmc_params* h, const wz_rational* a
  * is -(1/V) sum_x (m^* phi^* + g^* phi^*2).  F receives (re, im) per member of
  * the context (2 doubles for a single lattice).  Synchronous. */
 int wz_aux_vev(wz_ctx* ctx, double* F);
+
+/* Broken supersymmetric Ward-Takahashi identity of Eq. exid at the context's phi.
+ * Summed over x the variation density of the action is the cubic form of
+ * Eq. nzav; with the fermions integrated out (Majorana propagator M^-1 C^-1,
+ * C = gamma_0 gamma_2) and the fermion summed over the lattice (a uniform source:
+ * four solves of M psi_b = C^-1 e_b, one per spin column b) both sides are
+ * per-configuration 4 x 4 complex matrices, the common sqrt 2 left out:
+ *   WL[a][b] = (sum_x F~(x)) C[a][b]
+ *   WR[a][b] = sum_x [g (2 phi (D1 phi) P_+ + phi^2 D1 P_+) psi_b
+ *                     + g^* (2 phi^* (D1 phi^*) P_- + phi^*2 D1 P_-) psi_b]_a
+ * with D1 the gamma-odd part of the overlap (on the scalar: sum_mu gamma_mu
+ * F^-1[i sin p_mu / omega F phi], periodic).  The identity is <WR> = <WL>.
+ * WR, WL: 32 host doubles each, row-major [a][b], (re, im).  flags: WZ_SOLVE_MIXED
+ * or 0 (FP64 solves to true residual tol).  Synchronous. */
+int wz_ward_identity(wz_ctx* ctx, double tol, int maxiter, unsigned flags, double* WR, double* WL,
+                     wz_solve_stats* stats);
 
 /* Locality probe of Dslash (Sec. 3.2, Eq. uir): psi = Dslash eta for a unit
  * point source eta (spin 0 at the origin); f[r] = max ||psi(x)|| over the sites

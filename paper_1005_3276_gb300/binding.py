@@ -18,10 +18,10 @@ LIBPATH = os.path.join(HERE, "libwz.so")
 WZ_OK, WZ_EINVAL, WZ_ENOMEM, WZ_ECUDA, WZ_NOT_CONVERGED, WZ_EUNSUPPORTED = range(6)
 WZ_C64, WZ_C128 = 0, 1
 (WZ_OP_M, WZ_OP_MDAG, WZ_OP_MDAGM, WZ_OP_DSLASH, WZ_OP_M0INV, WZ_OP_M0INV_DAG,
- WZ_OP_MTILDE, WZ_OP_MTILDE_DAG, WZ_OP_MTILDE_DAGM) = range(9)
+ WZ_OP_MTILDE, WZ_OP_MTILDE_DAG, WZ_OP_MTILDE_DAGM, WZ_OP_D1) = range(10)
 OPS = {"M": WZ_OP_M, "Mdag": WZ_OP_MDAG, "MdagM": WZ_OP_MDAGM, "Dslash": WZ_OP_DSLASH,
        "M0inv": WZ_OP_M0INV, "M0inv_dag": WZ_OP_M0INV_DAG, "Mtilde": WZ_OP_MTILDE,
-       "Mtilde_dag": WZ_OP_MTILDE_DAG, "Mtilde_dagM": WZ_OP_MTILDE_DAGM}
+       "Mtilde_dag": WZ_OP_MTILDE_DAG, "Mtilde_dagM": WZ_OP_MTILDE_DAGM, "D1": WZ_OP_D1}
 
 
 class WzParams(ctypes.Structure):
@@ -148,6 +148,8 @@ def _load():
                            ctypes.POINTER(D), ctypes.POINTER(WzSolveStats)], I),
         "wz_rhmc_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzRational),
                                 ctypes.POINTER(WzRational), ctypes.POINTER(WzTrajStats)], I),
+        "wz_ward_identity": ([P, D, I, ctypes.c_uint, ctypes.POINTER(D), ctypes.POINTER(D),
+                              ctypes.POINTER(WzSolveStats)], I),
         "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
         "wz_locality": ([P, ctypes.POINTER(D), I], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
@@ -168,7 +170,7 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_trajectory", "wz_batch_create", "wz_batch_destroy", "wz_batch_last_error", "wz_batch_size",
            "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
            "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
-           "wz_rhmc_force", "wz_rhmc_trajectory",
+           "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity",
            "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
@@ -365,6 +367,16 @@ def wz_rhmc_trajectory(ctx, params, action, heatbath):
     return st.as_dict()
 
 
+def wz_ward_identity(ctx, tol=1e-12, maxiter=100000, mixed=False):
+    """(W_R, W_L) of Eq. exid at the context's phi, 4 x 4 complex numpy arrays, and solve stats."""
+    wr, wl = (ctypes.c_double * 32)(), (ctypes.c_double * 32)()
+    st = WzSolveStats()
+    check(ctx, LIB.wz_ward_identity(ctx, float(tol), int(maxiter), WZ_SOLVE_MIXED if mixed else 0, wr, wl,
+                                    ctypes.byref(st)))
+    to = lambda a: (np.array(a[0::2]) + 1j * np.array(a[1::2])).reshape(4, 4)
+    return to(wr), to(wl), st.as_dict()
+
+
 def wz_aux_vev(ctx, nm=1):
     """(1/V) sum_x F~(x) per member, as a list of complex numbers."""
     out = (ctypes.c_double * (2 * nm))()
@@ -452,6 +464,9 @@ class Lattice:
 
     def rhmc_trajectory(self, action, heatbath, **kw):
         return wz_rhmc_trajectory(self.ctx, hmc_params(**kw), action, heatbath)
+
+    def ward_identity(self, tol=1e-12, maxiter=100000, mixed=False):
+        return wz_ward_identity(self.ctx, tol, maxiter, mixed)
 
     def aux_vev(self):
         return wz_aux_vev(self.ctx)[0]

@@ -63,8 +63,8 @@ bool zt_supported(int nz, int nt) {
 struct TableArgs {
   int T, Z, Y, X;
   double r, M0, m2, invV;
-  double *hV, *hdV, *dV, *d2sV, *ksV;
-  float *hVf, *hdVf, *dVf, *d2sVf, *ksVf;
+  double *hV, *hdV, *dV, *d2sV, *ksV, *w1V, *w1sV;
+  float *hVf, *hdVf, *dVf, *d2sVf, *ksVf, *w1Vf, *w1sVf;
 };
 
 __global__ void momentum_tables_kernel(TableArgs a) {
@@ -92,9 +92,11 @@ __global__ void momentum_tables_kernel(TableArgs a) {
     a.hV[j] = h * a.invV;
     a.hdV[j] = h / den * a.invV;
     a.dV[j] = a.invV / den;
+    a.w1V[j] = a.invV / omega;
     a.hVf[j] = (float)a.hV[j];
     a.hdVf[j] = (float)a.hdV[j];
     a.dVf[j] = (float)a.dV[j];
+    a.w1Vf[j] = (float)a.w1V[j];
     // scalar symbols on the periodic grid (p_t = 2 pi nt / T): D2 = 1 - b/omega,
     // K = 1 - D2/2 (Eq. acws); at the zone corners sum sin^2 = 0 and omega = |b|
     double s2p = 0.0, wp = 0.0;
@@ -111,12 +113,14 @@ __global__ void momentum_tables_kernel(TableArgs a) {
     a.ksV[j] = (1.0 - 0.5 * D2) * a.invV;
     a.d2sVf[j] = (float)a.d2sV[j];
     a.ksVf[j] = (float)a.ksV[j];
+    a.w1sV[j] = a.invV / op;  // op >= 1 at the zone corners (b odd there)
+    a.w1sVf[j] = (float)a.w1sV[j];
   }
 }
 
-// per-axis tables: [sinT(T) sinZ(Z) sinY(Y) sinX(X) twc(T) tws(T)]
+// per-axis tables: [sinT(T) sinZ(Z) sinY(Y) sinX(X) twc(T) tws(T) ones(T) zeros(T)]
 __global__ void axis_tables_kernel(int T, int Z, int Y, int X, double* d, float* f) {
-  const int n = 3 * T + Z + Y + X;
+  const int n = 5 * T + Z + Y + X;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     double v;
     if (i < T) {
@@ -129,8 +133,12 @@ __global__ void axis_tables_kernel(int T, int Z, int Y, int X, double* d, float*
       v = sinpi(2.0 * (i - T - Z - Y) / X);
     } else if (i < 2 * T + Z + Y + X) {
       v = cospi((double)(i - (T + Z + Y + X)) / T);
-    } else {
+    } else if (i < 3 * T + Z + Y + X) {
       v = sinpi((double)(i - (2 * T + Z + Y + X)) / T);
+    } else if (i < 4 * T + Z + Y + X) {
+      v = 1.0;
+    } else {
+      v = 0.0;
     }
     d[i] = v;
     f[i] = (float)v;
@@ -143,19 +151,23 @@ template <typename R> static void carve(Tables<R>& t, R* base, long V, int T, in
   t.dV = base + 2 * V;
   t.d2sV = base + 3 * V;
   t.ksV = base + 4 * V;
-  R* ax = base + 5 * V;
+  t.w1V = base + 5 * V;
+  t.w1sV = base + 6 * V;
+  R* ax = base + 7 * V;
   t.sinT = ax;
   t.sinZ = ax + T;
   t.sinY = ax + T + Z;
   t.sinX = ax + T + Z + Y;
   t.twc = ax + T + Z + Y + X;
   t.tws = ax + 2 * T + Z + Y + X;
+  t.twc1 = ax + 3 * T + Z + Y + X;
+  t.tws0 = ax + 4 * T + Z + Y + X;
 }
 
 static int build_tables(wz_ctx* c) {
   const long V = c->V;
-  const long naxis = 3L * c->T + c->Z + c->Y + c->X;
-  const long n = 5 * V + naxis;
+  const long naxis = 5L * c->T + c->Z + c->Y + c->X;
+  const long n = 7 * V + naxis;
   WZ_CUDA_TRY(c, cudaMalloc(&c->t64.block, n * sizeof(double)));
   WZ_CUDA_TRY(c, cudaMalloc(&c->t32.block, n * sizeof(float)));
   carve(c->t64, (double*)c->t64.block, V, c->T, c->Z, c->Y, c->X);
@@ -174,6 +186,10 @@ static int build_tables(wz_ctx* c) {
   a.dV = c->t64.dV;
   a.d2sV = c->t64.d2sV;
   a.ksV = c->t64.ksV;
+  a.w1V = c->t64.w1V;
+  a.w1sV = c->t64.w1sV;
+  a.w1Vf = c->t32.w1V;
+  a.w1sVf = c->t32.w1sV;
   a.hVf = c->t32.hV;
   a.hdVf = c->t32.hdV;
   a.dVf = c->t32.dV;
@@ -437,10 +453,10 @@ int wz_set_phi(wz_ctx* c, const void* phi) { return set_member_phi(c, 0, phi); }
 int wz_apply(wz_ctx* c, int op, int dtype, const void* in, void* out, int nrhs, double shift) {
   if (!c) return WZ_EINVAL;
   if (!in || !out || nrhs < 0) return set_error(c, WZ_EINVAL, "wz_apply: bad argument");
-  if (op < WZ_OP_M || op > WZ_OP_MTILDE_DAGM) return set_error(c, WZ_EINVAL, "wz_apply: unknown op");
+  if (op < WZ_OP_M || op > WZ_OP_D1) return set_error(c, WZ_EINVAL, "wz_apply: unknown op");
   if (nrhs == 0) return WZ_OK;
   if (c->nm > 1 && nrhs % c->nm) return set_error(c, WZ_EINVAL, "wz_apply: nrhs must be a multiple of the members");
-  if (!c->same_mass && op >= WZ_OP_M0INV && op != WZ_OP_DSLASH)
+  if (!c->same_mass && op >= WZ_OP_M0INV && op != WZ_OP_DSLASH && op != WZ_OP_D1)
     return set_error(c, WZ_EINVAL, "wz_apply: M0^-1 operators need one mass for all members");
   if (dtype == WZ_C128) return apply_typed<double>(c, op, in, out, nrhs, shift);
   if (dtype == WZ_C64) return apply_typed<float>(c, op, in, out, nrhs, shift);

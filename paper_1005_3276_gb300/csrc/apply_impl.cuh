@@ -140,6 +140,16 @@ int apply_op(wz_ctx* c, int op, const cplx<R>* in, cplx<R>* out, int nrhs, R shi
       WZ_RUN(zt(ZT_DSLASH, R(1)));
       WZ_RUN(inv(XY_INV, nullptr, nullptr, out, nullptr));
       break;
+    case WZ_OP_D1: {
+      // the Dslash multiply with 1/omega in place of h: D1(p) = i gamma.sin p / omega
+      WZ_RUN(fwd(XY_FWD, in));
+      ZTArgs<R> za = zt_args<R>(c, R(1));
+      za.A = A;
+      za.hV = tables<R>(c).w1V;
+      WZ_RUN(launch_zt<R>(c->Z, c->T, ZT_DSLASH, za, nrhs, st));
+      WZ_RUN(inv(XY_INV, nullptr, nullptr, out, nullptr));
+      break;
+    }
     case WZ_OP_M0INV:
     case WZ_OP_M0INV_DAG:
       WZ_RUN(fwd(XY_FWD, in));

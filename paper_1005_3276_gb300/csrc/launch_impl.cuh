@@ -135,8 +135,8 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   const long grid = (long)nrhs * a.ntiles;
   if (grid == 0) return cudaSuccess;
   // the map covers right-hand sides 0 .. rhs0 + nrhs - 1 of A; the last one is reused
-  const R* t0 = MUL == ZT_DSLASH ? a.hV : (MUL == ZT_SCALAR ? a.d2sV : a.hdV);
-  const R* t1 = MUL == ZT_DSLASH ? nullptr : (MUL == ZT_SCALAR ? a.ksV : a.dV);
+  const R* t0 = (MUL == ZT_DSLASH || MUL == ZT_GRAD) ? a.hV : (MUL == ZT_SCALAR ? a.d2sV : a.hdV);
+  const R* t1 = (MUL == ZT_DSLASH || MUL == ZT_GRAD) ? nullptr : (MUL == ZT_SCALAR ? a.ksV : a.dV);
   struct MapCache {
     const void* A = nullptr;
     const void* t0 = nullptr;
@@ -182,6 +182,9 @@ cudaError_t launch_zt_p(int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) 
     case ZT_M0INV_DAG: return launch_zt_t<R, NZ, NT, ZT_M0INV_DAG>(a, nrhs, st);
     case ZT_SCALAR:
       if constexpr (sizeof(R) == 8) return launch_zt_t<R, NZ, NT, ZT_SCALAR>(a, nrhs, st);
+      break;
+    case ZT_GRAD:
+      if constexpr (sizeof(R) == 8) return launch_zt_t<R, NZ, NT, ZT_GRAD>(a, nrhs, st);
       break;
   }
   return cudaErrorInvalidValue;

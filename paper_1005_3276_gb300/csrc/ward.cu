@@ -1,0 +1,260 @@
+// Broken supersymmetric Ward-Takahashi identity of Eq. exid, per configuration.
+//
+// Summed over x, the variation density of the action is the cubic expression
+// of Eq. nzav; with the fermions integrated out at fixed phi (Majorana
+// propagator <chi(z) chi^T(y)> = M^-1 C^-1) and the fermion summed over y, both
+// sides are per-configuration quantities (the common sqrt 2 left out):
+//
+//   W_L[a][b] = (sum_x F~(x)) C[a][b]
+//   W_R[a][b] = sum_x [Kop psi_b]_a(x),  psi_b = M^-1 C^-1 u_b,  u_b(x) = e_b
+//   Kop psi  = g (2 phi (D1 phi) P_+ psi + phi^2 D1 P_+ psi)
+//            + g^* (2 phi^* (D1 phi^*) P_- psi + phi^*2 D1 P_- psi)
+//
+// D1 on spinors is the Dslash multiply with 1/omega in place of h (WZ_OP_D1);
+// D1 on a periodic scalar f is sum_mu gamma_mu f_mu with f_mu = F^-1[i sin p_mu /
+// omega F f], computed as one FP64 plane-pass transform of f copied into the
+// four slots (zt mode ZT_GRAD).  D1 maps P_+ into P_- and back, so D1 P_+ psi =
+// P_- D1 psi and D1 P_- psi = P_+ D1 psi: one D1 application per column.
+// The identity states <W_R> = <W_L>; in the continuum both vanish.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "apply_impl.cuh"
+#include "solver.h"
+#include "wz_probe.h"
+
+namespace wz {
+
+namespace {
+
+struct C4 {
+  double re[4][4], im[4][4];
+};
+
+// chiral basis of Sec. 2.1: gamma_0 = [[0, 1], [1, 0]], gamma_k = [[0, i sigma_k], [-i sigma_k, 0]]
+void gamma_matrix(int mu, C4* g) {
+  memset(g, 0, sizeof(*g));
+  // sigma_k as (re, im) 2x2
+  const double s_re[3][2][2] = {{{0, 1}, {1, 0}}, {{0, 0}, {0, 0}}, {{1, 0}, {0, -1}}};
+  const double s_im[3][2][2] = {{{0, 0}, {0, 0}}, {{0, -1}, {1, 0}}, {{0, 0}, {0, 0}}};
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      if (mu == 0) {
+        g->re[i][2 + j] = g->re[2 + i][j] = (i == j) ? 1.0 : 0.0;
+      } else {
+        const int k = mu - 1;
+        // upper right: i sigma = (-Im sigma, Re sigma); lower left: -i sigma
+        g->re[i][2 + j] = -s_im[k][i][j];
+        g->im[i][2 + j] = s_re[k][i][j];
+        g->re[2 + i][j] = s_im[k][i][j];
+        g->im[2 + i][j] = -s_re[k][i][j];
+      }
+    }
+}
+
+void mat_mul(const C4& a, const C4& b, C4* c) {
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      double r = 0, m = 0;
+      for (int k = 0; k < 4; ++k) {
+        r += a.re[i][k] * b.re[k][j] - a.im[i][k] * b.im[k][j];
+        m += a.re[i][k] * b.im[k][j] + a.im[i][k] * b.re[k][j];
+      }
+      c->re[i][j] = r;
+      c->im[i][j] = m;
+    }
+}
+
+// C = gamma_0 gamma_2; real orthogonal in this basis, so C^-1 = C^T
+void charge_conjugation(C4* C, C4* Cinv) {
+  C4 g0, g2;
+  gamma_matrix(0, &g0);
+  gamma_matrix(2, &g2);
+  mat_mul(g0, g2, C);
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      Cinv->re[i][j] = C->re[j][i];
+      Cinv->im[i][j] = -C->im[j][i];
+    }
+}
+
+struct Sources {
+  double re[4][4], im[4][4];  // [b][s]: spin s of the uniform source of column b
+};
+
+// out[b][x][s] = source[b][s] for every site x
+__global__ void uniform_sources(cplx<double>* out, long V, Sources src) {
+  const int b = blockIdx.y;
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 4 * V; i += (long)gridDim.x * blockDim.x) {
+    const int s = (int)(i & 3);
+    out[(long)b * 4 * V + i] = cplx<double>{src.re[b][s], src.im[b][s]};
+  }
+}
+
+// out[x][mu] = f(x) (or f^*) for the four slots of the gradient transform
+__global__ void copy_to_slots(const cplx<double>* f, int conjugate, cplx<double>* out, long V) {
+  for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < 4 * V; i += (long)gridDim.x * blockDim.x) {
+    const cplx<double> v = f[i >> 2];
+    out[i] = conjugate ? conj(v) : v;
+  }
+}
+
+// Block partials of sum_x [Kop psi_b]_a(x), grid (nblk, 4 columns b):
+// part[((b * nblk) + block) * 4 + a] (complex).
+__global__ void ward_contract(const cplx<double>* phi, const cplx<double>* psi, const cplx<double>* d1psi,
+                              const cplx<double>* f, const cplx<double>* fs, cplx<double> g, long V,
+                              cplx<double>* part) {
+  __shared__ double red[33];
+  const int b = blockIdx.y;
+  const cplx<double> I{0.0, 1.0};
+  cplx<double> acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+  for (long x = blockIdx.x * (long)blockDim.x + threadIdx.x; x < V; x += (long)gridDim.x * blockDim.x) {
+    const cplx<double> ph = phi[x], phs = conj(ph);
+    const cplx<double>* p = psi + ((long)b * V + x) * 4;
+    const cplx<double>* d = d1psi + ((long)b * V + x) * 4;
+    const cplx<double>* fx = f + x * 4;
+    const cplx<double>* fsx = fs + x * 4;
+    // (D1 phi) P_+ psi = sum_mu f_mu gamma_mu (0, 0, p2, p3): upper components
+    const cplx<double> gp0 = fx[0] * p[2] + fx[1] * (I * p[3]) + fx[2] * p[3] + fx[3] * (I * p[2]);
+    const cplx<double> gp1 = fx[0] * p[3] + fx[1] * (I * p[2]) - fx[2] * p[2] - fx[3] * (I * p[3]);
+    // (D1 phi^*) P_- psi = sum_mu fs_mu gamma_mu (p0, p1, 0, 0): lower components
+    const cplx<double> gm2 = fsx[0] * p[0] - fsx[1] * (I * p[1]) - fsx[2] * p[1] - fsx[3] * (I * p[0]);
+    const cplx<double> gm3 = fsx[0] * p[1] - fsx[1] * (I * p[0]) + fsx[2] * p[0] + fsx[3] * (I * p[1]);
+    const cplx<double> two{2.0, 0.0};
+    const cplx<double> gs = conj(g);
+    acc[0] = acc[0] + g * (two * ph * gp0 + (ph * ph) * d[0]);  // D1 P_+ psi = P_- D1 psi
+    acc[1] = acc[1] + g * (two * ph * gp1 + (ph * ph) * d[1]);
+    acc[2] = acc[2] + gs * (two * phs * gm2 + (phs * phs) * d[2]);  // D1 P_- psi = P_+ D1 psi
+    acc[3] = acc[3] + gs * (two * phs * gm3 + (phs * phs) * d[3]);
+  }
+  for (int a = 0; a < 4; ++a) {
+    const double sr = block_sum(acc[a].x, red);
+    __syncthreads();
+    const double si = block_sum(acc[a].y, red);
+    __syncthreads();
+    if (threadIdx.x == 0) part[((long)b * gridDim.x + blockIdx.x) * 4 + a] = cplx<double>{sr, si};
+  }
+}
+
+// D1 phi (or D1 phi^*) components: out[x][mu] = F^-1[i sin p_mu / omega F f](x), periodic grid
+int scalar_d1(wz_ctx* c, int conjugate, cplx<double>* slots, cplx<double>* out, cplx<double>* A) {
+  const long V = c->V;
+  count_launch();
+  copy_to_slots<<<(unsigned)((4 * V + 255) / 256 < 4096 ? (4 * V + 255) / 256 : 4096), 256, 0, c->stream>>>(
+      c->phi64, conjugate, slots, V);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  XYArgs<double> xa = xy_args<double>(c, 1);
+  xa.twc = c->t64.twc1;  // a periodic field: no antiperiodic twist
+  xa.tws = c->t64.tws0;
+  xa.kArr = c->k64;
+  xa.rpm = 1;
+  xa.nplanes = c->T * c->Z;
+  xa.psi = slots;
+  xa.A_out = A;
+  WZ_CUDA_TRY(c, launch_xy<double>(c->X, XY_FWD, xa, c->stream));
+  ZTArgs<double> za = zt_args<double>(c, 1.0);
+  za.A = A;
+  za.hV = c->t64.w1sV;
+  WZ_CUDA_TRY(c, launch_zt<double>(c->Z, c->T, ZT_GRAD, za, 1, c->stream));
+  XYArgs<double> xi = xa;
+  xi.A_in = A;
+  xi.A_out = nullptr;
+  xi.psi = nullptr;
+  xi.v_out = out;
+  WZ_CUDA_TRY(c, launch_xy<double>(c->X, XY_INV, xi, c->stream));
+  return WZ_OK;
+}
+
+}  // namespace
+
+}  // namespace wz
+
+using namespace wz;
+
+extern "C" int wz_ward_identity(wz_ctx* c, double tol, int maxiter, unsigned flags, double* WR, double* WL,
+                                wz_solve_stats* stats) {
+  if (!c) return WZ_EINVAL;
+  if (!WR || !WL || tol <= 0.0 || maxiter < 1) return set_error(c, WZ_EINVAL, "wz_ward_identity: bad argument");
+  if (c->nm != 1) return set_error(c, WZ_EINVAL, "wz_ward_identity: single-lattice context expected");
+  const auto t0 = std::chrono::steady_clock::now();
+  const long V = c->V;
+  const size_t f4 = sizeof(cplx<double>) * 4 * (size_t)V;
+  // workspace: sources / M^dag sources (4), psi (4), D1 psi (4), two gradient fields, slots
+  const size_t need = f4 * (4 + 4 + 4 + 2 + 1);
+  WZ_CUDA_TRY(c, c->ws_force.reserve(need));
+  cplx<double>* src = (cplx<double>*)c->ws_force.ptr;
+  cplx<double>* psi = src + 4 * 4 * V;
+  cplx<double>* d1psi = psi + 4 * 4 * V;
+  cplx<double>* fgrad = d1psi + 4 * 4 * V;
+  cplx<double>* fsgrad = fgrad + 4 * V;
+  cplx<double>* slots = fsgrad + 4 * V;
+  WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_MDAG, 4)));
+  cplx<double>* A = (cplx<double>*)c->ws_apply.ptr;
+
+  // uniform sources C^-1 e_b, then psi_b = M^-1 C^-1 u_b = (M^dag M)^-1 M^dag C^-1 u_b
+  C4 C, Cinv;
+  charge_conjugation(&C, &Cinv);
+  Sources so{};
+  for (int b = 0; b < 4; ++b)
+    for (int s = 0; s < 4; ++s) {
+      so.re[b][s] = Cinv.re[s][b];
+      so.im[b][s] = Cinv.im[s][b];
+    }
+  count_launch();
+  uniform_sources<<<dim3(256, 4), 256, 0, c->stream>>>(psi, V, so);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  int rc = apply_op<double>(c, WZ_OP_MDAG, psi, src, 4, 0.0, A);
+  if (rc) return rc;
+  SolveOut sol;
+  rc = (flags & WZ_SOLVE_MIXED) ? solve_impl<float>(c, src, psi, 4, single_shift(0.0), tol, maxiter, false, 0.1, &sol)
+                                : solve_impl<double>(c, src, psi, 4, single_shift(0.0), tol, maxiter, false, 0.0, &sol);
+  if (rc && rc != WZ_NOT_CONVERGED) return rc;
+  const int solve_rc = rc;
+  rc = apply_op<double>(c, WZ_OP_D1, psi, d1psi, 4, 0.0, A);
+  if (rc) return rc;
+  if ((rc = scalar_d1(c, 0, slots, fgrad, A))) return rc;
+  if ((rc = scalar_d1(c, 1, slots, fsgrad, A))) return rc;
+
+  const int nblk = 128;
+  WZ_CUDA_TRY(c, c->ws_red.reserve(sizeof(cplx<double>) * 4 * 4 * nblk));
+  count_launch();
+  ward_contract<<<dim3(nblk, 4), 256, 0, c->stream>>>(c->phi64, psi, d1psi, fgrad, fsgrad,
+                                                       cplx<double>{c->p.g_re, c->p.g_im}, V,
+                                                       (cplx<double>*)c->ws_red.ptr);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  std::vector<cplx<double>> h(4 * 4 * nblk);
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->ws_red.ptr, sizeof(cplx<double>) * h.size(), cudaMemcpyDeviceToHost,
+                                 c->stream));
+  WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      double sr = 0.0, si = 0.0;
+      for (int k = 0; k < nblk; ++k) {
+        sr += h[((long)b * nblk + k) * 4 + a].x;
+        si += h[((long)b * nblk + k) * 4 + a].y;
+      }
+      WR[2 * (a * 4 + b)] = sr;
+      WR[2 * (a * 4 + b) + 1] = si;
+    }
+  // left side: (sum_x F~) C
+  double F[2];
+  if ((rc = wz_aux_vev(c, F))) return rc;
+  const double fr = F[0] * (double)V, fi = F[1] * (double)V;
+  for (int a = 0; a < 4; ++a)
+    for (int b = 0; b < 4; ++b) {
+      WL[2 * (a * 4 + b)] = fr * C.re[a][b] - fi * C.im[a][b];
+      WL[2 * (a * 4 + b) + 1] = fr * C.im[a][b] + fi * C.re[a][b];
+    }
+  if (stats) {
+    stats->iterations = sol.iterations;
+    stats->total_iterations = sol.total_iterations;
+    stats->reliable_updates = sol.reliable_updates;
+    stats->converged = sol.converged;
+    stats->max_true_residual = sol.max_true_residual;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  if (solve_rc == WZ_NOT_CONVERGED) return set_error(c, WZ_NOT_CONVERGED, "wz_ward_identity: solve reached maxiter");
+  return WZ_OK;
+}

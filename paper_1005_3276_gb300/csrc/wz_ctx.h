@@ -21,12 +21,16 @@ template <typename R> struct Tables {
   R* dV = nullptr;
   R* d2sV = nullptr;  // scalar D2(p)/V, periodic grid (Eq. acws)
   R* ksV = nullptr;   // scalar K(p)/V = (1 - D2/2)/V
+  R* w1V = nullptr;   // 1/(omega(p) V), fermion grid: D1(p) = i gamma.sin p / omega
+  R* w1sV = nullptr;  // 1/(omega(p) V), periodic (scalar) grid
   R* sinT = nullptr;
   R* sinZ = nullptr;
   R* sinY = nullptr;
   R* sinX = nullptr;
   R* twc = nullptr;
   R* tws = nullptr;
+  R* twc1 = nullptr;  // identity twist (cos = 1, sin = 0): xy passes of periodic scalar fields
+  R* tws0 = nullptr;
   void* block = nullptr;  // single allocation holding everything above
 };
 

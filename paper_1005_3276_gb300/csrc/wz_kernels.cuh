@@ -321,6 +321,8 @@ enum ZTMul {
   ZT_M0INV,        // out = (-Dslash + m^* P_+ + m P_-) / den  in
   ZT_M0INV_DAG,    // out = ( Dslash + m P_+ + m^* P_-) / den  in
   ZT_SCALAR,       // periodic scalar pair packed in spin slots: slot 0 *= D2(p), slot 1 *= K(p)
+  ZT_GRAD,         // periodic scalar copied into the four slots: slot mu *= i sin p_mu / omega(p)
+                   // (the components of D1 acting on a scalar field; table in hV = 1/(omega V))
 };
 
 template <typename R> struct ZTArgs {
@@ -389,7 +391,7 @@ template <typename R, int NZ, int NT, int MUL> struct ZTSmem {
   static constexpr bool STAGE_TAB = sizeof(R) == 4;
   static constexpr int CB = (int)(C * sizeof(R)) >= 16 ? C : (int)(16 / sizeof(R));  // box columns
   static_assert(CB % C == 0, "a tile's columns must fall inside one table box");
-  static constexpr int NTAB = STAGE_TAB ? (MUL == ZT_DSLASH ? 1 : 2) : 0;
+  static constexpr int NTAB = STAGE_TAB ? ((MUL == ZT_DSLASH || MUL == ZT_GRAD) ? 1 : 2) : 0;
   static constexpr unsigned tab = NZ * NT * CB * sizeof(R);
   static constexpr unsigned tab_stride = (tab + 127) & ~127u;  // every box starts 128-byte aligned
   static constexpr unsigned tab_off = (tile + 127) & ~127u;
@@ -503,6 +505,12 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
       if constexpr (MUL == ZT_SCALAR) {
         const R sc = s == 0 ? (ZS::NTAB ? tab0[tix] : a.d2sV[pidx]) : (s == 1 ? (ZS::NTAB ? tab1[tix] : a.ksV[pidx]) : R(0));
         v[pt] = sc * v[pt];
+      } else if constexpr (MUL == ZT_GRAD) {
+        // periodic momenta: sin(2 pi pt / T) from the twiddle table; slot s is direction mu = s (t, x, y, z)
+        static_assert(WZ_TW_N % NT == 0, "periodic momenta must lie on the twiddle grid");
+        const R stp = Tw<R>::cosk((pt * (WZ_TW_N / NT) + 3 * WZ_TW_N / 4) % WZ_TW_N);
+        const R smu = s == 0 ? stp : (s == 1 ? sx : (s == 2 ? sy : sz));
+        v[pt] = (smu * (ZS::NTAB ? tab0[tix] : a.hV[pidx])) * mul_i(v[pt]);
       } else if constexpr (MUL == ZT_DSLASH) {
         const R hh = a.sign * (ZS::NTAB ? tab0[tix] : a.hV[pidx]);
         v[pt] = hh * mul_i(g);

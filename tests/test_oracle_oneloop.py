@@ -1,0 +1,48 @@
+"""Pins of the one-loop lattice sums (Sec. 5, Tables sse, fse, ase).
+
+* Both two-point functions vanish at zero external momentum, as the paper
+  states (N(k, 0) = 0 for the scalar; an odd integrand for the fermion).
+* The continuum limit: 1/r(k)^2 -> 1/(k^2 + m^2)^2, whose integral grows like
+  -2 ln(m a) / (16 pi^2); the scalar and fermion counterterms grow with the
+  coefficient the paper fits (0.00604 and 0.00597 per ln(ma), against
+  1/(16 pi^2) = 0.00633).
+* The printed finite-size tables at the coarse spacings (the formulas are
+  partly garbled in the source, so agreement is stated, not assumed): the
+  auxiliary at ma = 0.5 within 0.3%, the scalar at ma = 0.25 within 0.2%.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import oneloop
+
+
+def test_zero_momentum_vanishes():
+    sig_phi, sig_chi = oneloop.self_energies_at(8, 0.5, (0.0, 0.0, 0.0, 0.0))
+    assert abs(sig_phi) < 1e-15
+    assert max(abs(v) for v in sig_chi) < 1e-15
+
+
+@pytest.fixture(scope="module")
+def mL8():
+    """mL = 8 sums at ma = 0.5, 0.25, 0.125 (N = 16, 32, 64)."""
+    return {ma: oneloop.sums(int(round(8 / ma)), ma) for ma in (0.5, 0.25, 0.125)}
+
+
+def test_log_slopes(mL8):
+    a, b = mL8[0.25], mL8[0.125]
+    slope = [(b[i] - a[i]) / np.log(0.5) for i in range(3)]  # d Z / d ln(ma)
+    assert slope[2] == pytest.approx(-2.0 / (16 * np.pi ** 2), rel=0.15)
+    assert slope[0] == pytest.approx(0.00604, rel=0.25)
+    assert slope[1] == pytest.approx(0.00597, rel=0.25)
+
+
+def test_printed_values(mL8):
+    """Entries of the mL = 8 columns the formulas reproduce (others differ by up
+    to 7%, see the readings)."""
+    assert mL8[0.5][2] == pytest.approx(0.082542, rel=3e-3)     # auxiliary, Table ase
+    assert mL8[0.25][0] == pytest.approx(-0.009532, rel=2e-3)   # scalar, Table sse
+    assert mL8[0.125][0] == pytest.approx(-0.013358, rel=2e-3)
+    assert mL8[0.125][1] == pytest.approx(-0.011406, rel=2e-3)  # fermion, Table fse
+    for z in mL8.values():
+        assert z[0] < 0 and z[1] < 0 and z[2] > 0

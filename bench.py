@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true", help="skip the L = 8, 16, 32 apply sweep")
     ap.add_argument("--batch", action="store_true", help="also time the 64-lattice batched workload")
     ap.add_argument("--no-rhmc", action="store_true", help="skip the rational heatbath / RHMC timings")
+    ap.add_argument("--no-oneloop", action="store_true", help="skip the one-loop lattice sums (Sec. 5 tables)")
     ap.add_argument("--rhmc-fp64", action="store_true", help="also time the RHMC trajectory with FP64 solves")
     return ap.parse_args()
 
@@ -398,6 +399,25 @@ def main():
                                          "accept": [x["accept"] for x in sts]}
         tl.close()
 
+    # one-loop counterterms of Tables sse, fse, ase at mL = 8 (N = 8 / ma up to 1024),
+    # FP64 on the device, beside the paper's printed mL = 8 columns
+    oneloop = None
+    if not args.no_oneloop:
+        paper = {0.5: (-0.006355, -0.004027, 0.082542), 0.25: (-0.009532, -0.006973, 0.088658),
+                 0.125: (-0.013358, -0.011406, 0.095266), 0.0625: (-0.017541, -0.015632, 0.105719),
+                 0.03125: (-0.021837, -0.019965, 0.11255), 0.015625: (-0.026205, -0.024336, 0.13276),
+                 0.0078125: (-0.030583, -0.028720, 0.140261)}
+        oneloop = {"workload": "Z - 1 over |g|^2 at p = (0,0,0,2 pi/N), N = 8/ma, FP64", "rows": []}
+        for ma, ref in paper.items():
+            N = int(round(8.0 / ma))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            z = wz.wz_one_loop(N, ma)
+            dt = time.perf_counter() - t0
+            oneloop["rows"].append({"ma": ma, "N": N, "Z_phi": z[0], "Z_chi": z[1], "Z_F": z[2],
+                                    "paper_mL8": ref, "seconds": dt,
+                                    "terms_per_s": N ** 4 / 48.0 / dt})
+
     # apply-throughput sweep: (M^dag M) on L^4, FP32 vs FP64 fields, about 1M
     # site-RHS per launch sequence (256 / 16 / 1 right-hand sides at L = 8/16/32)
     sweep = None
@@ -520,7 +540,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
         }))
     lat.close()

@@ -289,6 +289,17 @@ int wz_ward_identity(wz_ctx* ctx, double tol, int maxiter, unsigned flags, doubl
  * T/2 + Z/2 + Y/2 + X/2 + 1 entries (nf); FP64.  Synchronous. */
 int wz_locality(wz_ctx* ctx, double* f, int nf);
 
+/* ---- one-loop lattice sums (Sec. 5, Tables sse, fse, ase) ----
+ *
+ * Counterterms over |g|^2 on an N^4 momentum lattice (a = 1, N even, 4 <= N <=
+ * 4096, k periodic), bare mass ma (mL = N ma), external momentum
+ * p = (0, 0, 0, 2 pi / N): z[0] = Z_phi - 1 = Sigma_phi(p) / sin^2(2 pi/N),
+ * z[1] = Z_chi - 1 = -Sigma_chi(p)_3 / sin(2 pi/N), z[2] = Z_F - 1 = Sigma_F(0),
+ * with the integrands of Sec. 5.2 (P = sin k, M = 1 - 2 sum sin^2(k/2),
+ * s = sqrt(P^2 + M^2), r = 2(1 - M/s) + (ma^2/2)(1 + M/s)).  FP64 on the current
+ * device, no context; synchronous.  WZ_EINVAL on bad arguments. */
+int wz_one_loop(int N, double ma, double* z);
+
 /* ---- batches of independent lattices (replicas of uneven extent and coupling) ----
  *
  * A batch holds n lattices, each with its own dims, m, g and phi (e.g. the

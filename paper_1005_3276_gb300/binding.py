@@ -150,6 +150,7 @@ def _load():
                                 ctypes.POINTER(WzRational), ctypes.POINTER(WzTrajStats)], I),
         "wz_ward_identity": ([P, D, I, ctypes.c_uint, ctypes.POINTER(D), ctypes.POINTER(D),
                               ctypes.POINTER(WzSolveStats)], I),
+        "wz_one_loop": ([I, D, ctypes.POINTER(D)], I),
         "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
         "wz_locality": ([P, ctypes.POINTER(D), I], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
@@ -170,7 +171,7 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_trajectory", "wz_batch_create", "wz_batch_destroy", "wz_batch_last_error", "wz_batch_size",
            "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
            "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
-           "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity",
+           "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity", "wz_one_loop",
            "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
@@ -375,6 +376,15 @@ def wz_ward_identity(ctx, tol=1e-12, maxiter=100000, mixed=False):
                                     ctypes.byref(st)))
     to = lambda a: (np.array(a[0::2]) + 1j * np.array(a[1::2])).reshape(4, 4)
     return to(wr), to(wl), st.as_dict()
+
+
+def wz_one_loop(N, ma):
+    """(Z_phi - 1, Z_chi - 1, Z_F - 1) / |g|^2 of the one-loop sums on N^4 momenta."""
+    z = (ctypes.c_double * 3)()
+    rc = LIB.wz_one_loop(int(N), float(ma), z)
+    if rc != WZ_OK:
+        raise WzError(rc, "wz_one_loop failed")
+    return tuple(z)
 
 
 def wz_aux_vev(ctx, nm=1):

@@ -6,9 +6,10 @@
   -2 ln(m a) / (16 pi^2); the scalar and fermion counterterms grow with the
   coefficient the paper fits (0.00604 and 0.00597 per ln(ma), against
   1/(16 pi^2) = 0.00633).
-* The printed finite-size tables at the coarse spacings (the formulas are
-  partly garbled in the source, so agreement is stated, not assumed): the
-  auxiliary at ma = 0.5 within 0.3%, the scalar at ma = 0.25 within 0.2%.
+* The printed mL = 8 columns: scalar and fermion entries at ma = 0.25 and
+  0.125 within 0.2% (the device sums reproduce the finer entries, N up to 1024,
+  to 1e-4 or better); the auxiliary column agrees at ma = 0.5 only (0.3%) and
+  drifts to a few percent at finer spacing, which is listed as a reading.
 """
 
 import numpy as np
@@ -46,3 +47,4 @@ def test_printed_values(mL8):
     assert mL8[0.125][1] == pytest.approx(-0.011406, rel=2e-3)  # fermion, Table fse
     for z in mL8.values():
         assert z[0] < 0 and z[1] < 0 and z[2] > 0
+

@@ -52,7 +52,8 @@ enum wz_status {
   WZ_ENOMEM = 2,          /* device allocation failed */
   WZ_ECUDA = 3,           /* CUDA runtime error (message in wz_last_error) */
   WZ_NOT_CONVERGED = 4,   /* solver hit maxiter; x holds the best iterate, stats filled */
-  WZ_EUNSUPPORTED = 5     /* combination not built (e.g. an extent without kernels) */
+  WZ_EUNSUPPORTED = 5,    /* combination not built (e.g. an extent without kernels) */
+  WZ_ETIMEOUT = 6         /* a bounded device-side wait (staged copy) ran out; outputs undefined */
 };
 
 enum wz_dtype { WZ_C64 = 0, WZ_C128 = 1 };
@@ -230,6 +231,10 @@ int wz_get_phi(wz_ctx* ctx, void* phi);
  * Synchronous.  WZ_NOT_CONVERGED if a solve hit its iteration cap. */
 int wz_force(wz_ctx* ctx, const void* eta, int npf, double tol, unsigned parts, void* grad, double* S_B,
              double* S_pf, wz_solve_stats* stats);
+
+/* S_B and S_pf (either may be NULL, not both) at the context's phi: the actions
+ * of wz_force without the gradient.  Synchronous. */
+int wz_action(wz_ctx* ctx, const void* eta, int npf, double tol, double* S_B, double* S_pf, wz_solve_stats* stats);
 
 /* Molecular dynamics of length h->tau in h->nsteps steps from (phi, pi) with
  * fixed pseudofermions eta (npf, complex128): phi (context) and pi (complex128

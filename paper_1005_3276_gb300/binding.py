@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libwz.so")
 
-WZ_OK, WZ_EINVAL, WZ_ENOMEM, WZ_ECUDA, WZ_NOT_CONVERGED, WZ_EUNSUPPORTED = range(6)
+WZ_OK, WZ_EINVAL, WZ_ENOMEM, WZ_ECUDA, WZ_NOT_CONVERGED, WZ_EUNSUPPORTED, WZ_ETIMEOUT = range(7)
 WZ_C64, WZ_C128 = 0, 1
 (WZ_OP_M, WZ_OP_MDAG, WZ_OP_MDAGM, WZ_OP_DSLASH, WZ_OP_M0INV, WZ_OP_M0INV_DAG,
  WZ_OP_MTILDE, WZ_OP_MTILDE_DAG, WZ_OP_MTILDE_DAGM, WZ_OP_D1) = range(10)
@@ -126,6 +126,7 @@ def _load():
         "wz_get_phi": ([P, P], I),
         "wz_force": ([P, P, I, D, ctypes.c_uint, P, ctypes.POINTER(D), ctypes.POINTER(D),
                       ctypes.POINTER(WzSolveStats)], I),
+        "wz_action": ([P, P, I, D, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(WzSolveStats)], I),
         "wz_md_integrate": ([P, P, P, I, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
         "wz_trajectory": ([P, ctypes.POINTER(WzHmcParams), ctypes.POINTER(WzTrajStats)], I),
         "wz_batch_create": ([ctypes.POINTER(WzParams), I, P, ctypes.POINTER(P)], I),
@@ -167,7 +168,7 @@ def _load():
 LIB = _load()
 
 EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "wz_set_phi", "wz_apply",
-           "wz_solve", "wz_apply_mdagm_noalloc", "wz_get_phi", "wz_force", "wz_md_integrate",
+           "wz_solve", "wz_apply_mdagm_noalloc", "wz_get_phi", "wz_force", "wz_action", "wz_md_integrate",
            "wz_trajectory", "wz_batch_create", "wz_batch_destroy", "wz_batch_last_error", "wz_batch_size",
            "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
            "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
@@ -281,6 +282,14 @@ def wz_force(ctx, eta, npf, grad, tol=1e-10, parts=WZ_FORCE_FERMION | WZ_FORCE_B
     sb, spf, st = ctypes.c_double(), ctypes.c_double(), WzSolveStats()
     check(ctx, LIB.wz_force(ctx, pe, int(npf), float(tol), int(parts), pg, ctypes.byref(sb),
                             ctypes.byref(spf), ctypes.byref(st)))
+    return sb.value, spf.value, st.as_dict()
+
+
+def wz_action(ctx, eta, npf, tol=1e-10):
+    """(S_B, S_pf, solve stats) at the context's phi."""
+    pe = field_ptr(eta, WZ_C128)[0] if npf > 0 else ctypes.c_void_p(0)
+    sb, spf, st = ctypes.c_double(), ctypes.c_double(), WzSolveStats()
+    check(ctx, LIB.wz_action(ctx, pe, int(npf), float(tol), ctypes.byref(sb), ctypes.byref(spf), ctypes.byref(st)))
     return sb.value, spf.value, st.as_dict()
 
 
@@ -474,6 +483,9 @@ class Lattice:
 
     def rhmc_trajectory(self, action, heatbath, **kw):
         return wz_rhmc_trajectory(self.ctx, hmc_params(**kw), action, heatbath)
+
+    def action(self, eta, npf, tol=1e-10):
+        return wz_action(self.ctx, eta, npf, tol)
 
     def ward_identity(self, tol=1e-12, maxiter=100000, mixed=False):
         return wz_ward_identity(self.ctx, tol, maxiter, mixed)

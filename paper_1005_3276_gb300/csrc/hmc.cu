@@ -546,7 +546,8 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st, const 
   if (graph)
     count_launch(c->traj_graph.outer_launches + hc[2] * c->traj_graph.body_launches +
                  hc[4] * c->traj_graph.body_launches_h);
-  if (hc[WZ_COUNTER_DEVICE_ERROR]) return set_error(c, WZ_ECUDA, "trajectory: a device-side copy wait ran out");
+  if (hc[WZ_COUNTER_DEVICE_ERROR])
+    return set_error(c, (int)(hc[WZ_COUNTER_DEVICE_ERROR] & 0xffffffffu), "trajectory: a device-side staged copy failed");
   const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   for (int j = 0; st && j < nm; ++j) {
     st[j].H0 = hres[5 * j + 0];
@@ -632,6 +633,37 @@ int wz_md_integrate(wz_ctx* c, void* pi, const void* eta, int npf, const wz_hmc_
     st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return WZ_OK;
+}
+
+int wz_action(wz_ctx* c, const void* eta, int npf, double tol, double* S_B, double* S_pf, wz_solve_stats* stats) {
+  if (!c) return WZ_EINVAL;
+  if (npf < 0 || (npf > 0 && !eta) || tol <= 0.0 || (!S_B && !S_pf))
+    return set_error(c, WZ_EINVAL, "wz_action: bad argument");
+  if (c->nm != 1) return set_error(c, WZ_EINVAL, "wz_action: single-lattice context expected");
+  const auto t0 = std::chrono::steady_clock::now();
+  const size_t f4 = sizeof(cplx<double>) * 4 * (size_t)c->V, f1 = f4 / 4;
+  WZ_CUDA_TRY(c, c->ws_stage.reserve(f4 * npf + f1));
+  char* stage = (char*)c->ws_stage.ptr;
+  const cplx<double>* e = (const cplx<double>*)eta;
+  if (npf > 0 && !is_device_pointer(eta)) {
+    WZ_CUDA_TRY(c, cudaMemcpyAsync(stage, eta, f4 * npf, cudaMemcpyHostToDevice, c->stream));
+    e = (const cplx<double>*)stage;
+  }
+  cplx<double>* grad = (cplx<double>*)(stage + f4 * npf);  // the gradient is computed and dropped
+  const unsigned parts = (S_pf && npf > 0 ? WZ_FORCE_FERMION : 0u) | (S_B ? WZ_FORCE_BOSON : 0u);
+  SolveOut so;
+  int rc = force_impl(c, e, npf, tol, parts, grad, S_B, S_pf, &so);
+  if (rc && rc != WZ_NOT_CONVERGED) return rc;
+  if (S_pf && npf == 0) *S_pf = 0.0;
+  if (stats) {
+    stats->iterations = so.iterations;
+    stats->total_iterations = so.total_iterations;
+    stats->reliable_updates = so.reliable_updates;
+    stats->converged = so.converged;
+    stats->max_true_residual = so.max_true_residual;
+    stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  return rc;
 }
 
 static bool rational_ok(const wz_rational* r) {

@@ -550,7 +550,9 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
 #undef WZ_RUN
 
   for (int j = 0; j < nrhs; ++j)
-    if (hst[j].status == WZ_ECUDA) return set_error(c, WZ_ECUDA, "solver: a staged bulk copy did not complete");
+    if (hst[j].status == WZ_ETIMEOUT || hst[j].status == WZ_ECUDA)
+      return set_error(c, hst[j].status, hst[j].status == WZ_ETIMEOUT ? "solver: a staged copy wait ran out"
+                                                                       : "solver: a staged copy was misaligned");
   SolveOut o;
   for (int j = 0; j < nrhs; ++j) {
     o.iterations = hst[j].iters > o.iterations ? hst[j].iters : o.iterations;

@@ -243,7 +243,7 @@ xy_cg(CGArgs<R, LO> a) {
   auto stage_failed = [&](bool ok) -> bool {
     if (!__syncthreads_or(!ok)) return false;
     if (threadIdx.x == 0) {
-      st->status = WZ_ECUDA;
+      st->status = WZ_ETIMEOUT;
       st->run = 0;
       st->ru = 0;
       st->active = 0;

@@ -88,7 +88,7 @@ template <typename R> struct XYArgs {
   int Z;                 // planes per time slice (plane = t * Z + z)
   const R* twc;          // cos(pi t / T): antiperiodic twist, applied in position space
   const R* tws;          // sin(pi t / T)
-  int* fail;             // set to WZ_ECUDA if a staged copy did not complete (may be null)
+  int* fail;             // set to WZ_ETIMEOUT if a staged copy did not complete (may be null)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
 };
@@ -219,7 +219,7 @@ xy_pass(XYArgs<R> a) {
       }
     }
     if (__syncthreads_or(!mbar_wait_bounded(bar, 0))) {
-      if (tid == 0 && a.fail) *a.fail = WZ_ECUDA;
+      if (tid == 0 && a.fail) *a.fail = WZ_ETIMEOUT;
       mbar_wait_bounded(bar, 0);
       return;
     }
@@ -344,7 +344,7 @@ template <typename R> struct ZTArgs {
   int X, XY;
   const int* gate;     // optional per-RHS run flag: block returns if gate[rhs * gate_stride] == 0
   int gate_stride;
-  int* fail;           // set to WZ_ECUDA at fail[rhs * fail_stride] if the tile copy did not complete
+  int* fail;           // WZ_ETIMEOUT (copy wait ran out) or WZ_ECUDA (misaligned tile) at fail[rhs * fail_stride]
   int fail_stride;
   int rhs0;            // first right-hand side of this launch (launches may cover a group of RHS)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
@@ -448,7 +448,7 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
     if constexpr (ZS::NTAB >= 2) tma_load_3d(smem_raw + ZS::tab_off + ZS::tab_stride, &tmT1, tx0, 0, 0, &bar);
   }
   if (__syncthreads_or(!mbar_wait_bounded(&bar, 0))) {
-    if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ECUDA;
+    if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ETIMEOUT;
     mbar_wait_bounded(&bar, 0);
     return;
   }

@@ -228,3 +228,16 @@ def test_trajectory_graph_equals_eager(wz, monkeypatch):
         lat.close()
     assert runs["0"][0] == runs["1"][0]
     assert np.array_equal(runs["0"][1], runs["1"][1])
+
+
+def test_action_matches_force_actions(wz):
+    dims = (8, 8, 8, 8)
+    P = oracle.Params(dims=dims, m=0.3, g=0.4)
+    phi = synth.scalar_field(dims, 0.5, 12)
+    eta = synth.spinor_rhs(2, dims, 13)
+    lat = wz.Lattice(dims, m=P.m, g=P.g)
+    lat.set_phi(phi)
+    sb, spf, _ = lat.action(eta, 2, tol=1e-12)
+    assert abs(sb - oforce.bosonic_action(P, phi)) <= 1e-12 * abs(sb)
+    ref = sum(oforce.pf_action(P, phi, e, tol=1e-13) for e in eta)
+    assert abs(spf - ref) <= 1e-9 * abs(ref)

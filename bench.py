@@ -108,14 +108,15 @@ def oracle_applies_per_s(w, seconds):
     return n / dt, n, dt
 
 
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "zt_pass_fp32_16x4_12rhs.traffic.txt")
-TRAFFIC_SOURCES = ("wz_kernels.cuh", "wz_fft.cuh", "wz_tma.cuh", "launch_impl.cuh", "twiddles.h")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cg_passes_fp32_16x4_12rhs.traffic.txt")
+TRAFFIC_SOURCES = ("wz_kernels.cuh", "wz_cg.cuh", "wz_fft.cuh", "wz_tma.cuh", "launch_impl.cuh", "twiddles.h")
 
 
-def recorded_traffic(kind, real_bytes):
-    """DRAM bytes per launch of the zt pass from the committed ncu record, or None
-    if the probed kernel is another one or its sources changed since the capture."""
-    if kind != "zt" or real_bytes != 4:
+def recorded_traffic(kind, real_bytes, alg_bytes_per_launch):
+    """DRAM bytes per launch of a CG kernel class from the committed ncu record,
+    scaled to the launch's right-hand sides, or None if the record is for other
+    kernel sources or another class."""
+    if real_bytes != 4:
         return None
     try:
         rec = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line and not line.startswith("#"))
@@ -126,9 +127,10 @@ def recorded_traffic(kind, real_bytes):
     for f in TRAFFIC_SOURCES:
         with open(os.path.join(ROOT, "paper_1005_3276_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest()[:16] != rec.get("source_sha256_16", "").strip():
+    if h.hexdigest()[:16] != rec.get("source_sha256_16", "").strip() or kind not in rec:
         return None
-    return float(rec["traffic_bytes_per_launch"])
+    per_rhs, alg_per_rhs = (float(v) for v in rec[kind].split())
+    return per_rhs * alg_bytes_per_launch / alg_per_rhs
 
 
 def cpu_threads():
@@ -513,7 +515,9 @@ def main():
     roofline = {"bound": "hbm", "kernel": f"{dom} (FP{8 * args.probe_bytes})",
                 "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "peak_source": peak_src,
-                "traffic": recorded_traffic(dom, args.probe_bytes), "launches": probe["launches"],
+                "traffic": recorded_traffic(dom, args.probe_bytes,
+                                            probe["bytes"] / max(1, probe["launches"])),
+                "launches": probe["launches"],
                 "avg_launch_us": 1000.0 * probe["total_ms"] / max(1, probe["timed_launches"]),
                 "algorithmic_bytes_per_launch": probe["bytes"] / max(1, probe["launches"])}
 

@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batch", action="store_true", help="also time the 64-lattice batched workload")
     ap.add_argument("--no-rhmc", action="store_true", help="skip the rational heatbath / RHMC timings")
     ap.add_argument("--no-oneloop", action="store_true", help="skip the one-loop lattice sums (Sec. 5 tables)")
+    ap.add_argument("--large", action="store_true",
+                    help="also time the 32^4 large-lattice pieces (force evaluation, Ward identity, <F>)")
     ap.add_argument("--rhmc-fp64", action="store_true", help="also time the RHMC trajectory with FP64 solves")
     return ap.parse_args()
 
@@ -420,6 +422,38 @@ def main():
                                     "paper_mL8": ref, "seconds": dt,
                                     "terms_per_s": N ** 4 / 48.0 / dt})
 
+    # large single lattice: 32^4, m = 0.02, g = 1.0, hot start sigma 1, 4 pseudofermions.
+    # A whole trajectory (Omelyan, 40 steps = 81 force evaluations) is minutes; the
+    # pieces of one are timed: a force evaluation with its 4-RHS mixed solve, the
+    # Ward-identity measurement (4 uniform-source solves) and <F>.
+    large = None
+    if args.large:
+        lw = synth.LARGE_32
+        ll = wz.Lattice(lw.dims, m=lw.m, g=lw.g, stream=stream.cuda_stream)
+        ll.set_phi(torch.from_numpy(synth.scalar_field(lw.dims, lw.sigma, 0)).cuda())
+        eta = torch.from_numpy(synth.spinor_rhs(lw.nrhs, lw.dims, 1)).cuda()
+        G = torch.zeros(lw.dims, dtype=torch.complex128, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sb, spf, fst = ll.force(eta, G, tol=1e-10)
+        torch.cuda.synchronize()
+        t_force = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        WR, WL, wst = ll.ward_identity(tol=1e-10, mixed=True)
+        t_ward = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        F = ll.aux_vev()
+        t_aux = time.perf_counter() - t0
+        large = {"workload": f"{lw.name}: 32^4, m={lw.m}, g={lw.g}, phi sigma {lw.sigma}, {lw.nrhs} pseudofermions, "
+                             "mixed CG to 1e-10",
+                 "force_eval_s": t_force, "force_cg_iterations_max": fst["iterations"],
+                 "force_cg_iterations_total": fst["total_iterations"],
+                 "ward_s": t_ward, "ward_cg_iterations_max": wst["iterations"],
+                 "ward_R_trace": [float(np.trace(WR).real), float(np.trace(WR).imag)],
+                 "ward_L_00_01": [float(WL[0, 1].real), float(WL[0, 1].imag)],
+                 "aux_vev": [F.real, F.imag], "aux_s": t_aux}
+        ll.close()
+
     # apply-throughput sweep: (M^dag M) on L^4, FP32 vs FP64 fields, about 1M
     # site-RHS per launch sequence (256 / 16 / 1 right-hand sides at L = 8/16/32)
     sweep = None
@@ -544,7 +578,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "large": large, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
         }))
     lat.close()

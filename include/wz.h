@@ -278,7 +278,7 @@ int wz_aux_vev(wz_ctx* ctx, double* F);
  * C = gamma_0 gamma_2) and the fermion summed over the lattice (a uniform source:
  * four solves of M psi_b = C^-1 e_b, one per spin column b) both sides are
  * per-configuration 4 x 4 complex matrices, the common sqrt 2 left out:
- *   WL[a][b] = (sum_x F~(x)) C[a][b]
+ *   WL[a][b] = F_b C[a][b], F_b = sum_x F~ (b = 2, 3: P_+) or sum_x F~^* (b = 0, 1: P_-)
  *   WR[a][b] = sum_x [g (2 phi (D1 phi) P_+ + phi^2 D1 P_+) psi_b
  *                     + g^* (2 phi^* (D1 phi^*) P_- + phi^*2 D1 P_-) psi_b]_a
  * with D1 the gamma-odd part of the overlap (on the scalar: sum_mu gamma_mu

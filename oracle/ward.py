@@ -6,10 +6,11 @@ The identity relates the volume sum of the auxiliary field to the correlation
 of the variation density S(x) of the action (Eq. uity) with the fermion summed
 over the lattice.  The sum over x of S is the cubic expression of Eq. nzav, so
 that with the fermions integrated out at a fixed scalar field (Majorana
-propagator <chi(z) chi^T(y)> = (C M)^-1(z, y) = M^-1 C^-1) both sides are
-computable per configuration:
+propagator <chi(z) chi^T(y)> = -(C M)^-1(z, y) = -M^-1 C^-1 for the action's sign,
+see the readings) both sides are computable per configuration:
 
-    W_L[a, b] = (sum_x F~(x)) C[a, b],     F~ = -(1 - D2/2)(m^* phi^* + g^* phi^*2)
+    W_L[a, b] = F_b C[a, b],   F_b = sum_x F~ for b in P_+ (2, 3), sum_x F~^* for b in P_- (0, 1),
+                               F~ = -(1 - D2/2)(m^* phi^* + g^* phi^*2)
     W_R[a, b] = sum_x [ Kop psi_b ]_a(x),  psi_b = M^-1 C^-1 u_b,  u_b(x) = e_b at every x
     Kop psi   = g (2 phi (D1 phi) P_+ psi + phi^2 D1 P_+ psi)
               + g^* (2 phi^* (D1 phi^*) P_- psi + phi^*2 D1 P_- psi)
@@ -22,8 +23,12 @@ transformation (sqrt 2 on both sides) is left out.  The identity states
 <W_R> = <W_L> over the measure; in the continuum both vanish.
 
 Readings (the paper leaves them implicit): the sum over y of the fermion makes
-the source uniform, so no stochastic estimate is needed; the sign and the
-Grassmann ordering follow <chi_i chi_j> = (A^-1)_ij for exp(-chi^T A chi / 2).
+the source uniform, so no stochastic estimate is needed.  The left side is the
+contact term of the source derivative before the paper's abbreviation: the
+variation of chi~_b carries F~ in the P_+ rows and F~^* in the P_- rows.  With
+exp(-S) and S = -sum (1/2) chi^T C M chi + ..., <chi chi^T> = -M^-1 C^-1; that sign
+and C_ba = -C_ab make the identity <W_R> = <W_L> with W_R as defined (propagator
+M^-1 C^-1).
 """
 
 import numpy as np
@@ -89,6 +94,7 @@ def ward_right(params, phi, tol=1e-13):
 
 
 def ward_left(params, phi):
-    """W_L[a, b] = (sum_x F~(x)) C[a, b]; K(p = 0) = 1 makes sum_x F~ = -sum_x (m^* phi^* + g^* phi^*2)."""
+    """W_L[a, b] = F_b C[a, b]; K(p = 0) = 1 makes sum_x F~ = -sum_x (m^* phi^* + g^* phi^*2)."""
     Fsum = -np.sum(np.conj(params.m) * np.conj(phi) + np.conj(params.g) * np.conj(phi) ** 2)
-    return Fsum * CCONJ
+    Fb = np.array([np.conj(Fsum), np.conj(Fsum), Fsum, Fsum])
+    return CCONJ * Fb[None, :]

@@ -1,11 +1,12 @@
 // Broken supersymmetric Ward-Takahashi identity of Eq. exid, per configuration.
 //
 // Summed over x, the variation density of the action is the cubic expression
-// of Eq. nzav; with the fermions integrated out at fixed phi (Majorana
-// propagator <chi(z) chi^T(y)> = M^-1 C^-1) and the fermion summed over y, both
-// sides are per-configuration quantities (the common sqrt 2 left out):
+// of Eq. nzav; with the fermions integrated out at fixed phi and the fermion
+// summed over y, both sides are per-configuration quantities (the common sqrt 2
+// left out; the Majorana propagator is -M^-1 C^-1, and its sign together with
+// C^T = -C leaves M^-1 C^-1 in W_R):
 //
-//   W_L[a][b] = (sum_x F~(x)) C[a][b]
+//   W_L[a][b] = F_b C[a][b], F_b = sum_x F~ (b = 2, 3) or sum_x F~^* (b = 0, 1)
 //   W_R[a][b] = sum_x [Kop psi_b]_a(x),  psi_b = M^-1 C^-1 u_b,  u_b(x) = e_b
 //   Kop psi  = g (2 phi (D1 phi) P_+ psi + phi^2 D1 P_+ psi)
 //            + g^* (2 phi^* (D1 phi^*) P_- psi + phi^*2 D1 P_- psi)
@@ -238,12 +239,12 @@ extern "C" int wz_ward_identity(wz_ctx* c, double tol, int maxiter, unsigned fla
       WR[2 * (a * 4 + b)] = sr;
       WR[2 * (a * 4 + b) + 1] = si;
     }
-  // left side: (sum_x F~) C
+  // left side: F_b C[a][b], F_b = sum_x F~ for b in P_+ (2, 3), its conjugate for b in P_- (0, 1)
   double F[2];
   if ((rc = wz_aux_vev(c, F))) return rc;
-  const double fr = F[0] * (double)V, fi = F[1] * (double)V;
   for (int a = 0; a < 4; ++a)
     for (int b = 0; b < 4; ++b) {
+      const double fr = F[0] * (double)V, fi = (b >= 2 ? F[1] : -F[1]) * (double)V;
       WL[2 * (a * 4 + b)] = fr * C.re[a][b] - fi * C.im[a][b];
       WL[2 * (a * 4 + b) + 1] = fr * C.im[a][b] + fi * C.re[a][b];
     }

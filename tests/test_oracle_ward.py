@@ -81,4 +81,7 @@ def test_ward_left_is_the_auxiliary_sum():
     phi = synth.scalar_field(dims, 0.5, 5)
     from oracle import force
     V = int(np.prod(dims))
-    np.testing.assert_allclose(ward.ward_left(P, phi), V * force.auxiliary_vev(P, phi) * CCONJ, rtol=1e-13)
+    F = V * force.auxiliary_vev(P, phi)
+    WL = ward.ward_left(P, phi)
+    np.testing.assert_allclose(WL[:, 2:], F * CCONJ[:, 2:], rtol=1e-13)
+    np.testing.assert_allclose(WL[:, :2], np.conj(F) * CCONJ[:, :2], rtol=1e-13)

@@ -274,8 +274,9 @@ int wz_aux_vev(wz_ctx* ctx, double* F);
 
 /* Broken supersymmetric Ward-Takahashi identity of Eq. exid at the context's phi.
  * Summed over x the variation density of the action is the cubic form of
- * Eq. nzav; with the fermions integrated out (Majorana propagator M^-1 C^-1,
- * C = gamma_0 gamma_2) and the fermion summed over the lattice (a uniform source:
+ * Eq. nzav; with the fermions integrated out (Majorana propagator -M^-1 C^-1,
+ * C = gamma_0 gamma_2, whose sign and C^T = -C leave M^-1 C^-1 in WR) and the
+ * fermion summed over the lattice (a uniform source:
  * four solves of M psi_b = C^-1 e_b, one per spin column b) both sides are
  * per-configuration 4 x 4 complex matrices, the common sqrt 2 left out:
  *   WL[a][b] = F_b C[a][b], F_b = sum_x F~ (b = 2, 3: P_+) or sum_x F~^* (b = 0, 1: P_-)
@@ -287,6 +288,27 @@ int wz_aux_vev(wz_ctx* ctx, double* F);
  * or 0 (FP64 solves to true residual tol).  Synchronous. */
 int wz_ward_identity(wz_ctx* ctx, double tol, int maxiter, unsigned flags, double* WR, double* WL,
                      wz_solve_stats* stats);
+
+/* Correlators of the naive lattice supercurrent (Eq. latsuc) with the scalar and
+ * the fermion, Eq. sitre, at the context's phi, both x and y projected on zero
+ * spatial momentum.  The current is S_mu(x) = Gamma_mu(x) chi(x),
+ *   Gamma_mu = sqrt2 [(D1 phi) gamma_mu P_+ + (D1 phi^*) gamma_mu P_-
+ *                     + W' gamma_mu P_- + W'^* gamma_mu P_+],   W' = m phi + g phi^2,
+ * D1 on the scalar as in wz_ward_identity, and <chi(x) chi^T(z) C> = -M^-1(x, z).
+ * The source z is weighted by the caller's field w (a point, a wall or Gaussian
+ * noise with E[w(z) w^*(z')] = delta(z, z'), whose mean then sums all source
+ * positions):
+ *   psi_b = -M^-1 (w e_b)  (four solves, b = 0..3),   xi(t) = sum_zvec w(t, zvec)
+ *   Q_mu(t)[a][b] = sum_xvec [Gamma_mu psi_b]_a(t, xvec),   Phi_0(t) = sum_yvec phi, Phi_1 = Phi_0^*
+ *   R[s][mu][dx][dy][a][b] = sum_t' xi(t')^* sgn Phi_s(t' + dy) Q_mu(t' + dx)[a][b]
+ * with times mod T and sgn = -1 where t' + dx >= T (the antiperiodic fermion
+ * crossing the boundary), so dx, dy are sink times relative to the source.
+ * w: device pointer, complex128 [T][Z][Y][X] (not modified).  R: host, 2 * 4 * T
+ * * T * 16 complex (re, im interleaved) in the index order above.  flags:
+ * WZ_SOLVE_MIXED or 0.  Errors: WZ_EINVAL (null pointer, tol <= 0, maxiter < 1,
+ * batched context); WZ_NOT_CONVERGED (R from the best iterates).  Synchronous. */
+int wz_supercurrent(wz_ctx* ctx, const void* w, double tol, int maxiter, unsigned flags, double* R,
+                    wz_solve_stats* stats);
 
 /* Locality probe of Dslash (Sec. 3.2, Eq. uir): psi = Dslash eta for a unit
  * point source eta (spin 0 at the origin); f[r] = max ||psi(x)|| over the sites

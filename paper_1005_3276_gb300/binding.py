@@ -151,6 +151,7 @@ def _load():
                                 ctypes.POINTER(WzRational), ctypes.POINTER(WzTrajStats)], I),
         "wz_ward_identity": ([P, D, I, ctypes.c_uint, ctypes.POINTER(D), ctypes.POINTER(D),
                               ctypes.POINTER(WzSolveStats)], I),
+        "wz_supercurrent": ([P, P, D, I, ctypes.c_uint, ctypes.POINTER(D), ctypes.POINTER(WzSolveStats)], I),
         "wz_one_loop": ([I, D, ctypes.POINTER(D)], I),
         "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
         "wz_locality": ([P, ctypes.POINTER(D), I], I),
@@ -172,7 +173,7 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_trajectory", "wz_batch_create", "wz_batch_destroy", "wz_batch_last_error", "wz_batch_size",
            "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
            "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
-           "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity", "wz_one_loop",
+           "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity", "wz_supercurrent", "wz_one_loop",
            "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
 
 
@@ -387,6 +388,22 @@ def wz_ward_identity(ctx, tol=1e-12, maxiter=100000, mixed=False):
     return to(wr), to(wl), st.as_dict()
 
 
+def wz_supercurrent(ctx, w, T, tol=1e-12, maxiter=100000, mixed=False):
+    """R[s, mu, dx, dy, a, b] of the supercurrent correlators (Eq. sitre) for the
+    source weight w (complex128 (T, Z, Y, X), numpy or device tensor), and solve stats."""
+    ptr, dt = field_ptr(w)
+    if dt != WZ_C128:
+        raise ValueError("w must be complex128")
+    n = 2 * 4 * T * T * 16
+    buf = (ctypes.c_double * (2 * n))()
+    st = WzSolveStats()
+    check(ctx, LIB.wz_supercurrent(ctx, ptr, float(tol), int(maxiter),
+                                   WZ_SOLVE_MIXED if mixed else 0, buf, ctypes.byref(st)))
+    out = np.ctypeslib.as_array(buf)
+    R = (out[0::2] + 1j * out[1::2]).reshape(2, 4, T, T, 4, 4)
+    return R, st.as_dict()
+
+
 def wz_one_loop(N, ma):
     """(Z_phi - 1, Z_chi - 1, Z_F - 1) / |g|^2 of the one-loop sums on N^4 momenta."""
     z = (ctypes.c_double * 3)()
@@ -489,6 +506,9 @@ class Lattice:
 
     def ward_identity(self, tol=1e-12, maxiter=100000, mixed=False):
         return wz_ward_identity(self.ctx, tol, maxiter, mixed)
+
+    def supercurrent(self, w, tol=1e-12, maxiter=100000, mixed=False):
+        return wz_supercurrent(self.ctx, w, self.dims[0], tol, maxiter, mixed)
 
     def aux_vev(self):
         return wz_aux_vev(self.ctx)[0]

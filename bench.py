@@ -61,7 +61,8 @@ def parse():
     ap.add_argument("--no-rhmc", action="store_true", help="skip the rational heatbath / RHMC timings")
     ap.add_argument("--no-oneloop", action="store_true", help="skip the one-loop lattice sums (Sec. 5 tables)")
     ap.add_argument("--large", action="store_true",
-                    help="also time the 32^4 large-lattice pieces (force evaluation, Ward identity, <F>)")
+                    help="also time the 32^4 large-lattice pieces (force evaluation, Ward identity, <F>, "
+                         "supercurrent correlators)")
     ap.add_argument("--rhmc-fp64", action="store_true", help="also time the RHMC trajectory with FP64 solves")
     return ap.parse_args()
 
@@ -425,7 +426,8 @@ def main():
     # large single lattice: 32^4, m = 0.02, g = 1.0, hot start sigma 1, 4 pseudofermions.
     # A whole trajectory (Omelyan, 40 steps = 81 force evaluations) is minutes; the
     # pieces of one are timed: a force evaluation with its 4-RHS mixed solve, the
-    # Ward-identity measurement (4 uniform-source solves) and <F>.
+    # Ward-identity measurement (4 uniform-source solves), <F> and the supercurrent
+    # correlators on a Gaussian noise source (4 solves).
     large = None
     if args.large:
         lw = synth.LARGE_32
@@ -444,6 +446,11 @@ def main():
         t0 = time.perf_counter()
         F = ll.aux_vev()
         t_aux = time.perf_counter() - t0
+        # supercurrent correlators on one Gaussian noise source, E[w w^*] = 1 per site
+        wsrc = torch.from_numpy(synth.scalar_field(lw.dims, np.sqrt(0.5), 2)).cuda()
+        t0 = time.perf_counter()
+        Rsc, sst = ll.supercurrent(wsrc, tol=1e-10, mixed=True)
+        t_sc = time.perf_counter() - t0
         large = {"workload": f"{lw.name}: 32^4, m={lw.m}, g={lw.g}, phi sigma {lw.sigma}, {lw.nrhs} pseudofermions, "
                              "mixed CG to 1e-10",
                  "force_eval_s": t_force, "force_cg_iterations_max": fst["iterations"],
@@ -451,7 +458,10 @@ def main():
                  "ward_s": t_ward, "ward_cg_iterations_max": wst["iterations"],
                  "ward_R_trace": [float(np.trace(WR).real), float(np.trace(WR).imag)],
                  "ward_L_00_01": [float(WL[0, 1].real), float(WL[0, 1].imag)],
-                 "aux_vev": [F.real, F.imag], "aux_s": t_aux}
+                 "aux_vev": [F.real, F.imag], "aux_s": t_aux,
+                 "supercurrent_s": t_sc, "supercurrent_cg_iterations_max": sst["iterations"],
+                 "supercurrent_R0_mu0_dx1_dy0_trace": [float(np.trace(Rsc[0, 0, 1, 0]).real),
+                                                       float(np.trace(Rsc[0, 0, 1, 0]).imag)]}
         ll.close()
 
     # apply-throughput sweep: (M^dag M) on L^4, FP32 vs FP64 fields, about 1M

@@ -140,6 +140,16 @@ __global__ void ward_contract(const cplx<double>* phi, const cplx<double>* psi, 
   }
 }
 
+// W[a * 4 + b] = sum over the nblk block partials of column b, component a (fixed order)
+__global__ void ward_reduce(const cplx<double>* part, int nblk, cplx<double>* W) {
+  const int i = threadIdx.x;
+  if (i >= 16) return;
+  const int a = i / 4, b = i % 4;
+  cplx<double> s{0.0, 0.0};
+  for (int k = 0; k < nblk; ++k) s = s + part[((long)b * nblk + k) * 4 + a];
+  W[i] = s;
+}
+
 // D1 phi (or D1 phi^*) components: out[x][mu] = F^-1[i sin p_mu / omega F f](x), periodic grid
 int scalar_d1(wz_ctx* c, int conjugate, cplx<double>* slots, cplx<double>* out, cplx<double>* A) {
   const long V = c->V;
@@ -220,26 +230,19 @@ extern "C" int wz_ward_identity(wz_ctx* c, double tol, int maxiter, unsigned fla
   if ((rc = scalar_d1(c, 1, slots, fsgrad, A))) return rc;
 
   const int nblk = 128;
-  WZ_CUDA_TRY(c, c->ws_red.reserve(sizeof(cplx<double>) * 4 * 4 * nblk));
+  WZ_CUDA_TRY(c, c->ws_red.reserve(sizeof(cplx<double>) * (4 * 4 * nblk + 16)));
+  cplx<double>* part = (cplx<double>*)c->ws_red.ptr;
   count_launch();
   ward_contract<<<dim3(nblk, 4), 256, 0, c->stream>>>(c->phi64, psi, d1psi, fgrad, fsgrad,
-                                                       cplx<double>{c->p.g_re, c->p.g_im}, V,
-                                                       (cplx<double>*)c->ws_red.ptr);
+                                                       cplx<double>{c->p.g_re, c->p.g_im}, V, part);
   WZ_CUDA_TRY(c, cudaGetLastError());
-  std::vector<cplx<double>> h(4 * 4 * nblk);
-  WZ_CUDA_TRY(c, cudaMemcpyAsync(h.data(), c->ws_red.ptr, sizeof(cplx<double>) * h.size(), cudaMemcpyDeviceToHost,
+  count_launch();
+  ward_reduce<<<1, 32, 0, c->stream>>>(part, nblk, part + 4 * 4 * nblk);
+  WZ_CUDA_TRY(c, cudaGetLastError());
+  // row-major [a][b] complex is the (re, im) layout of WR
+  WZ_CUDA_TRY(c, cudaMemcpyAsync(WR, part + 4 * 4 * nblk, sizeof(cplx<double>) * 16, cudaMemcpyDeviceToHost,
                                  c->stream));
   WZ_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  for (int a = 0; a < 4; ++a)
-    for (int b = 0; b < 4; ++b) {
-      double sr = 0.0, si = 0.0;
-      for (int k = 0; k < nblk; ++k) {
-        sr += h[((long)b * nblk + k) * 4 + a].x;
-        si += h[((long)b * nblk + k) * 4 + a].y;
-      }
-      WR[2 * (a * 4 + b)] = sr;
-      WR[2 * (a * 4 + b) + 1] = si;
-    }
   // left side: F_b C[a][b], F_b = sum_x F~ for b in P_+ (2, 3), its conjugate for b in P_- (0, 1)
   double F[2];
   if ((rc = wz_aux_vev(c, F))) return rc;

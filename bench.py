@@ -141,6 +141,19 @@ def cpu_threads():
     return getattr(oracle_applies_per_s, "cores", 1)
 
 
+def combine_ranks(dist, total_ms, total_applies, device):
+    """Whole-job numbers of the replicas: the slowest rank's time and the work of
+    all ranks (identity without a process group)."""
+    if dist is None:
+        return total_ms, total_applies
+    import torch
+    t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    a = torch.tensor([float(total_applies)], dtype=torch.float64, device=device)
+    dist.all_reduce(a, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(a.item())
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -293,14 +306,7 @@ def main():
     dom = args.probe if args.probe != "auto" else max(probes, key=lambda k: probes[k]["total_ms"])
     probe = probes[dom]
 
-    # max time over ranks, sum of work over ranks
-    t_max, applies_all = total_ms, total_applies
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        a = torch.tensor([float(total_applies)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(a, op=dist.ReduceOp.SUM)
-        t_max, applies_all = float(t.item()), int(a.item())
+    t_max, applies_all = combine_ranks(dist, total_ms, total_applies, "cuda")
     value = applies_all / (t_max / 1000.0)
 
     # FP64 throughout, same workload (one solve)

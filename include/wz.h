@@ -53,7 +53,8 @@ enum wz_status {
   WZ_ECUDA = 3,           /* CUDA runtime error (message in wz_last_error) */
   WZ_NOT_CONVERGED = 4,   /* solver hit maxiter; x holds the best iterate, stats filled */
   WZ_EUNSUPPORTED = 5,    /* combination not built (e.g. an extent without kernels) */
-  WZ_ETIMEOUT = 6         /* a bounded device-side wait (staged copy) ran out; outputs undefined */
+  WZ_ETIMEOUT = 6,        /* a bounded device-side wait (staged copy) ran out; outputs undefined */
+  WZ_ENONFINITE = 7       /* a solver norm became NaN or Inf (non-finite phi, b or couplings); x undefined */
 };
 
 enum wz_dtype { WZ_C64 = 0, WZ_C128 = 1 };

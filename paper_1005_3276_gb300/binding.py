@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIBPATH = os.path.join(HERE, "libwz.so")
 
-WZ_OK, WZ_EINVAL, WZ_ENOMEM, WZ_ECUDA, WZ_NOT_CONVERGED, WZ_EUNSUPPORTED, WZ_ETIMEOUT = range(7)
+WZ_OK, WZ_EINVAL, WZ_ENOMEM, WZ_ECUDA, WZ_NOT_CONVERGED, WZ_EUNSUPPORTED, WZ_ETIMEOUT, WZ_ENONFINITE = range(8)
 WZ_C64, WZ_C128 = 0, 1
 (WZ_OP_M, WZ_OP_MDAG, WZ_OP_MDAGM, WZ_OP_DSLASH, WZ_OP_M0INV, WZ_OP_M0INV_DAG,
  WZ_OP_MTILDE, WZ_OP_MTILDE_DAG, WZ_OP_MTILDE_DAGM, WZ_OP_D1) = range(10)

@@ -549,10 +549,13 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   }
 #undef WZ_RUN
 
-  for (int j = 0; j < nrhs; ++j)
+  for (int j = 0; j < nrhs; ++j) {
     if (hst[j].status == WZ_ETIMEOUT || hst[j].status == WZ_ECUDA)
       return set_error(c, hst[j].status, hst[j].status == WZ_ETIMEOUT ? "solver: a staged copy wait ran out"
                                                                        : "solver: a staged copy was misaligned");
+    if (hst[j].status == WZ_ENONFINITE)
+      return set_error(c, WZ_ENONFINITE, "solver: a residual norm became NaN or Inf (non-finite input)");
+  }
   SolveOut o;
   for (int j = 0; j < nrhs; ++j) {
     o.iterations = hst[j].iters > o.iterations ? hst[j].iters : o.iterations;

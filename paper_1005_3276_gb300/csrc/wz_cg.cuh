@@ -67,7 +67,7 @@ struct RhsState {
   int active;      // not finished
   int iters;       // inner iterations
   int ru_count;    // reliable updates done (FP64 applies)
-  int status;      // WZ_OK or WZ_NOT_CONVERGED
+  int status;      // WZ_OK, WZ_NOT_CONVERGED, WZ_ENONFINITE (or a staged-copy error)
 };
 
 enum CGMode { CG_P1 = 0, CG_P3, CG_P5, RU_P1, RU_P5 };
@@ -487,9 +487,10 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
     s->iters = 0;
     s->ru_count = 0;
     s->ru = 0;
-    s->status = WZ_OK;
-    s->active = t > 0.0;
-    s->run = t > 0.0;
+    // a non-finite |b|^2 (NaN or Inf in the right-hand side) stops the system at once
+    s->status = isfinite(t) ? WZ_OK : WZ_ENONFINITE;
+    s->active = isfinite(t) && t > 0.0;
+    s->run = s->active;
   }
 }
 
@@ -503,6 +504,13 @@ static __global__ void cg_scalar_iter(RhsState* st, const double* part, const do
   // the alpha P5 used (the same sum, in the same order): pending for the next P1
   const double pAp = sum_partials(part_pAp + (long)blockIdx.x * nblk, nblk);
   if (threadIdx.x == 0) {
+    if (!isfinite(t) || !isfinite(pAp)) {  // NaN or Inf in the operator or the iterates
+      s->status = WZ_ENONFINITE;
+      s->run = 0;
+      s->ru = 0;
+      s->active = 0;
+      return;
+    }
     s->alpha = pAp > 0.0 ? s->rr / pAp : 0.0;
     s->iters += 1;
     if (counters) atomicAdd(&counters[0], 1ULL);
@@ -527,7 +535,11 @@ static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, 
     if (counters) atomicAdd(&counters[1], 1ULL);
     s->rtrue2 = t;
     s->alpha = 0.0;  // RU_P1 folded the pending update into x_hi
-    if (t <= s->tol2 * s->bnorm2) {
+    if (!isfinite(t)) {
+      s->active = 0;
+      s->run = 0;
+      s->status = WZ_ENONFINITE;
+    } else if (t <= s->tol2 * s->bnorm2) {
       s->active = 0;
       s->run = 0;
       s->status = WZ_OK;

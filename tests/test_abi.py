@@ -51,3 +51,27 @@ def test_create_rejects_bad_lattices(wz, dims, code):
     with pytest.raises(wz.WzError) as e:
         wz.wz_create(wz.make_params(dims))
     assert e.value.code == code
+
+
+def test_context_calls_reject_a_null_context(wz):
+    """Every context call checks its handle before touching the device."""
+    L = wz.LIB
+    n = None
+    calls = {
+        "wz_set_phi": lambda: L.wz_set_phi(n, n),
+        "wz_get_phi": lambda: L.wz_get_phi(n, n),
+        "wz_apply": lambda: L.wz_apply(n, 0, 1, n, n, 1, 0.0),
+        "wz_solve": lambda: L.wz_solve(n, n, n, 1, 0.0, 1e-10, 10, 0, n, n),
+        "wz_force": lambda: L.wz_force(n, n, 1, 1e-10, 3, n, n, n, n),
+        "wz_action": lambda: L.wz_action(n, n, 1, 1e-10, n, n, n),
+        "wz_trajectory": lambda: L.wz_trajectory(n, n, n),
+        "wz_ward_identity": lambda: L.wz_ward_identity(n, 1e-10, 10, 0, n, n, n),
+        "wz_supercurrent": lambda: L.wz_supercurrent(n, n, 1e-10, 10, 0, n, n),
+        "wz_aux_vev": lambda: L.wz_aux_vev(n, n),
+        "wz_locality": lambda: L.wz_locality(n, n, 0),
+        "wz_spectral_bounds": lambda: L.wz_spectral_bounds(n, n, n),
+        "wz_apply_mdagm_noalloc": lambda: L.wz_apply_mdagm_noalloc(n, 0, n, n, 1, 0.0),
+    }
+    for name, call in calls.items():
+        assert call() == wz.WZ_EINVAL, name
+    assert L.wz_destroy(n) == wz.WZ_OK

@@ -161,3 +161,28 @@ def test_graph_and_eager_launches_agree(wz, small, monkeypatch):
         xs.append(x)
         lat.close()
     assert torch.equal(xs[0], xs[1])
+
+
+@pytest.mark.parametrize("where", ["phi", "b"])
+@pytest.mark.parametrize("mixed", [True, False])
+def test_nonfinite_input_stops_with_status(wz, where, mixed):
+    """Host-side fault injection: a NaN in phi or an Inf in b ends the solve at
+    once with WZ_ENONFINITE (not after maxiter iterations, not as converged),
+    and the context keeps working."""
+    dims = (4, 4, 4, 4)
+    lat = wz.Lattice(dims, m=0.3, g=0.4)
+    phi = synth.scalar_field(dims, 0.5, 1)
+    b = synth.spinor_rhs(2, dims, 2)
+    if where == "phi":
+        phi[1, 2, 3, 0] = np.nan
+    else:
+        b[1, 0, 1, 2, 3, 1] = np.inf
+    lat.set_phi(phi)
+    x = np.zeros_like(b)
+    with pytest.raises(wz.WzError) as e:
+        lat.solve(b, x, tol=1e-10, maxiter=100000, mixed=mixed)
+    assert e.value.code == wz.WZ_ENONFINITE
+    lat.set_phi(synth.scalar_field(dims, 0.5, 1))
+    rc, st, _ = lat.solve(synth.spinor_rhs(2, dims, 2), x, tol=1e-10, mixed=mixed)
+    assert rc == wz.WZ_OK and st["converged"] == 2
+    lat.close()

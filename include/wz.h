@@ -391,6 +391,17 @@ typedef struct wz_probe_result {
 int wz_probe_begin(int kind, int real_bytes);
 int wz_probe_end(wz_probe_result* out);
 
+/* Self-test of the bounded device waits (the failure path behind WZ_ETIMEOUT):
+ * one block initialises an mbarrier, announces 16 transaction bytes that no
+ * copy delivers, and polls it with mbarrier.try_wait at most `polls` times
+ * (1 <= polls <= 65536; the staged passes use the same loop with
+ * WZ_MBAR_SPIN_LIMIT polls).  *status receives WZ_ETIMEOUT when the wait ran
+ * out as designed (WZ_OK would mean the phase completed); *cycles the SM clock
+ * cycles the polling took, from which the duration of the passes' limit
+ * follows.  No copy is issued and nothing is left in flight.  Runs on the
+ * current device, synchronous. */
+int wz_selftest_wait_timeout(int polls, int* status, long long* cycles);
+
 #ifdef __cplusplus
 }
 #endif

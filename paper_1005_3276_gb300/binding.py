@@ -156,6 +156,7 @@ def _load():
         "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
         "wz_locality": ([P, ctypes.POINTER(D), I], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
+        "wz_selftest_wait_timeout": ([I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)], I),
         "wz_probe_begin": ([I, I], I),
         "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
     }
@@ -174,7 +175,8 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_batch_groups", "wz_batch_set_phi", "wz_batch_get_phi", "wz_batch_solve", "wz_batch_trajectory",
            "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
            "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity", "wz_supercurrent", "wz_one_loop",
-           "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end")
+           "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end",
+           "wz_selftest_wait_timeout")
 
 
 def _is_torch(x):
@@ -426,6 +428,13 @@ def wz_locality(ctx, dims):
     out = (ctypes.c_double * n)()
     check(ctx, LIB.wz_locality(ctx, out, n))
     return np.array(list(out))
+
+
+def wz_selftest_wait_timeout(polls):
+    """(status, cycles) of the bounded-wait self-test: WZ_ETIMEOUT when the wait ran out."""
+    st, cyc = ctypes.c_int(-1), ctypes.c_longlong(0)
+    check(None, LIB.wz_selftest_wait_timeout(int(polls), ctypes.byref(st), ctypes.byref(cyc)))
+    return st.value, cyc.value
 
 
 def wz_kernel_launches():

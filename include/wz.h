@@ -304,10 +304,11 @@ int wz_ward_identity(wz_ctx* ctx, double tol, int maxiter, unsigned flags, doubl
  *   R[s][mu][dx][dy][a][b] = sum_t' xi(t')^* sgn Phi_s(t' + dy) Q_mu(t' + dx)[a][b]
  * with times mod T and sgn = -1 where t' + dx >= T (the antiperiodic fermion
  * crossing the boundary), so dx, dy are sink times relative to the source.
- * w: device pointer, complex128 [T][Z][Y][X] (not modified).  R: host, 2 * 4 * T
- * * T * 16 complex (re, im interleaved) in the index order above.  flags:
- * WZ_SOLVE_MIXED or 0.  Errors: WZ_EINVAL (null pointer, tol <= 0, maxiter < 1,
- * batched context); WZ_NOT_CONVERGED (R from the best iterates).  Synchronous. */
+ * w: complex128 [T][Z][Y][X], host or device (16-byte aligned), not modified.
+ * R: host, 2 * 4 * T * T * 16 complex (re, im interleaved) in the index order
+ * above.  flags: WZ_SOLVE_MIXED or 0.  Errors: WZ_EINVAL (null pointer, tol <= 0,
+ * maxiter < 1, misaligned w, batched context); WZ_NOT_CONVERGED (R from the best
+ * iterates); WZ_ENONFINITE (NaN or Inf in w or phi).  Synchronous. */
 int wz_supercurrent(wz_ctx* ctx, const void* w, double tol, int maxiter, unsigned flags, double* R,
                     wz_solve_stats* stats);
 

@@ -130,8 +130,10 @@ typedef struct wz_solve_stats {
  * is reported in stats).  b and x may be host or device pointers and must not
  * alias.  Synchronous: returns after the solution is in x.  Returns
  * WZ_NOT_CONVERGED (x = last iterate, stats filled) if maxiter inner
- * iterations did not suffice for some RHS.  resid (may be NULL) receives
- * nrhs FP64 true relative residuals of the original system. */
+ * iterations did not suffice for some RHS, WZ_ENONFINITE (x undefined) as soon
+ * as a norm of some RHS becomes NaN or Inf (non-finite b, phi or couplings).
+ * resid (may be NULL) receives nrhs FP64 true relative residuals of the
+ * original system. */
 int wz_solve(wz_ctx* ctx, const void* b, void* x, int nrhs, double shift, double tol, int maxiter,
              unsigned flags, wz_solve_stats* stats, double* resid);
 

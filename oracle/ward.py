@@ -28,7 +28,13 @@ contact term of the source derivative before the paper's abbreviation: the
 variation of chi~_b carries F~ in the P_+ rows and F~^* in the P_- rows.  With
 exp(-S) and S = -sum (1/2) chi^T C M chi + ..., <chi chi^T> = -M^-1 C^-1; that sign
 and C_ba = -C_ab make the identity <W_R> = <W_L> with W_R as defined (propagator
-M^-1 C^-1).
+M^-1 C^-1).  The printed Eq. exid carries the opposite sign; the pin below decides.
+
+Pins (tests/test_oracle_ward.py): W_R against a dense position-space route, its
+zero at g = 0, the scalar D1 of a plane wave, and the identity <W_R> = <W_L>
+itself over the exact measure Pf(CM) exp(-S_B) on a lattice where the
+reduction of Eq. nzav is exact (T = 3, periodic fermions), which fixes the
+sign and the chirality structure of W_L.
 """
 
 import numpy as np

@@ -48,8 +48,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wz", choices=["wz", "reference"])
-    ap.add_argument("--probe", default="auto", help="kernel class for the roofline (auto: the dominant one)")
-    ap.add_argument("--probe-bytes", type=int, default=4)
+    ap.add_argument("--probe", default="auto",
+                    help="kernel class for the roofline, e.g. zt_fp32 (auto: the one with the most time per solve)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison solve")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
@@ -114,13 +114,46 @@ def oracle_applies_per_s(w, seconds):
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "cg_passes_fp32_16x4_12rhs.traffic.txt")
 TRAFFIC_SOURCES = ("wz_kernels.cuh", "wz_cg.cuh", "wz_fft.cuh", "wz_tma.cuh", "launch_impl.cuh", "twiddles.h")
 
+# kernel classes of one mixed solve: FP32 iteration passes and the FP64
+# reliable-update passes (zt runs in both precisions)
+PROBE_CLASSES = (("zt", 4), ("cg_p1", 4), ("cg_p3", 4), ("cg_p5", 4), ("zt", 8), ("ru_p1", 8), ("ru_p5", 8))
 
-def recorded_traffic(kind, real_bytes, alg_bytes_per_launch):
-    """DRAM bytes per launch of a CG kernel class from the committed ncu record,
-    scaled to the launch's right-hand sides, or None if the record is for other
-    kernel sources or another class."""
-    if real_bytes != 4:
+
+def kernel_table(probes):
+    """Per kernel class: launches, timed launches, the average event time of a
+    timed launch, the algorithmic bytes of a timed launch, the achieved rate
+    (bytes / time over the same launches), the time per solve extrapolated to
+    every launch, and that time's share of the summed classes."""
+    out = {}
+    for k, v in probes.items():
+        timed = v["timed_launches"]
+        if timed <= 0 or v["total_ms"] <= 0:
+            out[k] = {"launches": v["launches"], "timed_launches": timed, "avg_launch_us": None,
+                      "algorithmic_bytes_per_launch": None, "achieved_GB_s": None, "ms_per_solve": 0.0}
+            continue
+        avg_ms = v["total_ms"] / timed
+        out[k] = {"launches": v["launches"], "timed_launches": timed, "avg_launch_us": 1000.0 * avg_ms,
+                  "algorithmic_bytes_per_launch": v["bytes"] / timed,
+                  "achieved_GB_s": v["bytes"] / (v["total_ms"] / 1000.0) / 1e9,
+                  "ms_per_solve": avg_ms * v["launches"]}
+    tot = sum(x["ms_per_solve"] for x in out.values())
+    for x in out.values():
+        x["share_of_probed_time"] = x["ms_per_solve"] / tot if tot > 0 else None
+    return out
+
+
+def dominant_class(kernels):
+    """The class with the largest extrapolated time per solve."""
+    return max(kernels, key=lambda k: kernels[k]["ms_per_solve"])
+
+
+def recorded_traffic(cls, probe, alg_bytes_per_launch):
+    """DRAM bytes per launch of an FP32 kernel class from the committed ncu
+    record, scaled to the launch's algorithmic bytes, or None if the record is
+    for other kernel sources or another class."""
+    if not cls.endswith("_fp32") or alg_bytes_per_launch is None:
         return None
+    kind = cls[:-len("_fp32")]
     try:
         rec = dict(line.split(":", 1) for line in open(TRAFFIC_FILE) if ":" in line and not line.startswith("#"))
     except OSError:
@@ -290,21 +323,18 @@ def main():
     launches = wz.wz_kernel_launches() - launches0
     clk = clocks.stop()
 
-    # Roofline of the dominant kernel: one more step of the same workload with
-    # the library's probe armed (CUDA events around every launch of the
-    # kernel class on the launching stream; the probe makes the solver launch
-    # its kernels one by one instead of replaying its graph, the kernels are
-    # the same).
+    # Roofline of the dominant kernel: one more solve of the same workload per
+    # kernel class with the library's probe armed (CUDA events around every
+    # launch of the class on its launching stream; the probe makes the solver
+    # launch its kernels one by one on one stream instead of replaying its
+    # graph -- the kernels are the same).
     probes = {}
-    for kind in ("zt", "cg_p1", "cg_p3", "cg_p5"):
+    for kind, rb in PROBE_CLASSES:
         flush.zero_()
         torch.cuda.synchronize()
-        wz.wz_probe_begin(kind, args.probe_bytes)
+        wz.wz_probe_begin(kind, rb)
         solve()
-        probes[kind] = wz.wz_probe_end()
-    # the dominant kernel class: largest summed launch time over one solve
-    dom = args.probe if args.probe != "auto" else max(probes, key=lambda k: probes[k]["total_ms"])
-    probe = probes[dom]
+        probes[f"{kind}_fp{8 * rb}"] = wz.wz_probe_end()
 
     t_max, applies_all = combine_ranks(dist, total_ms, total_applies, "cuda")
     value = applies_all / (t_max / 1000.0)
@@ -349,6 +379,13 @@ def main():
                           "cg_iterations_per_traj": float(np.mean([x["cg_iterations"] for x in sts])),
                           "dH": [round(x["dH"], 5) for x in sts], "accept": [x["accept"] for x in sts]}
         hmc["mixed_speedup"] = hmc["fp64"]["ms_per_traj"] / hmc["mixed"]["ms_per_traj"]
+        # the CG iterations of a trajectory as a whole-iteration HBM figure: one
+        # FP32 (FP64) iteration moves 18 spinor fields and phi twice per site
+        V = int(np.prod(hw.dims))
+        for label, bps in (("mixed", 18 * 32 + 2 * 8), ("fp64", 18 * 64 + 2 * 16)):
+            h = hmc[label]
+            h["cg_bytes_per_site_iteration"] = bps
+            h["cg_GB_s"] = h["cg_iterations_per_traj"] * bps * V / (h["ms_per_traj"] / 1000.0) / 1e9
         hlat.close()
 
     # rational heatbath eta = (M^dag M)^1/8 R of the paper's heatbath table: L^3 x 32,
@@ -557,19 +594,17 @@ def main():
     peak = peaks.get("hbm_gbs")
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
-    achieved = probe["bytes"] / (probe["total_ms"] / 1000.0) / 1e9 if probe["total_ms"] > 0 else None
-    kernels = {k: {"launches": v["launches"], "total_ms_per_solve": v["total_ms"],
-                   "avg_launch_us": 1000.0 * v["total_ms"] / max(1, v["timed_launches"]),
-                   "achieved_GB_s": v["bytes"] / (v["total_ms"] / 1000.0) / 1e9 if v["total_ms"] > 0 else None}
-               for k, v in probes.items()}
-    roofline = {"bound": "hbm", "kernel": f"{dom} (FP{8 * args.probe_bytes})",
-                "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "peak_source": peak_src,
-                "traffic": recorded_traffic(dom, args.probe_bytes,
-                                            probe["bytes"] / max(1, probe["launches"])),
-                "launches": probe["launches"],
-                "avg_launch_us": 1000.0 * probe["total_ms"] / max(1, probe["timed_launches"]),
-                "algorithmic_bytes_per_launch": probe["bytes"] / max(1, probe["launches"])}
+    kernels = kernel_table(probes)
+    dom = args.probe if args.probe != "auto" else dominant_class(kernels)
+    k = kernels[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": k["achieved_GB_s"], "peak": peak, "unit": "GB/s",
+                "frac": k["achieved_GB_s"] / peak if k["achieved_GB_s"] else None, "peak_source": peak_src,
+                "traffic": recorded_traffic(dom, probes[dom], k["algorithmic_bytes_per_launch"]),
+                "launches": k["launches"], "timed_launches": k["timed_launches"],
+                "avg_launch_us": k["avg_launch_us"],
+                "algorithmic_bytes_per_launch": k["algorithmic_bytes_per_launch"],
+                "note": "eager single-stream launches of one solve, CUDA events per launch; achieved = "
+                        "algorithmic bytes / event time over the same (timed) launches"}
 
     # the whole CG iteration against the same peak: per M^dag M apply of one RHS
     # the five passes move 18 FP32 spinor fields (P1 6, zt 2 + 2, P3 4, P5 4)
@@ -596,6 +631,10 @@ def main():
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
             "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "large": large, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
+            "hmc_traj_per_s": None if hmc is None else {
+                "mixed": hmc["mixed"]["traj_per_s"], "fp64": hmc["fp64"]["traj_per_s"],
+                "mixed_over_fp64": hmc["mixed_speedup"],
+                "mixed_cg_frac_of_hbm": hmc["mixed"]["cg_GB_s"] / peak, "workload": hmc["workload"]},
         }))
     lat.close()
     if dist is not None:

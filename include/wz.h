@@ -42,6 +42,8 @@
 #ifndef WZ_H
 #define WZ_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -94,6 +96,17 @@ int wz_destroy(wz_ctx* ctx);
 const char* wz_last_error(const wz_ctx* ctx);
 /* 1 if an extent n has compiled kernels (spatial / time), else 0. */
 int wz_supported_extent(int n);
+
+/* Workspace budget (not part of the method).  A context grows its device
+ * workspaces on demand: the solver's vectors, the apply intermediates, the
+ * force and HMC fields.  wz_set_workspace_limit caps their total in bytes
+ * (0 removes the cap).  A call that would need more returns WZ_ENOMEM, as
+ * when cudaMalloc runs out of device memory; the refused growth releases
+ * nothing, so the context stays usable for every call that fits.
+ * wz_workspace_bytes returns what the workspaces hold now (tables, phi and
+ * the caller's fields are not counted). */
+int wz_set_workspace_limit(wz_ctx* ctx, size_t bytes);
+size_t wz_workspace_bytes(const wz_ctx* ctx);
 
 /* Set the scalar field phi (complex128 [T][Z][Y][X], host or device).  The
  * context keeps an FP64 copy and an FP32 copy for the inner solver. */
@@ -380,16 +393,17 @@ unsigned long long wz_kernel_launches(void);
  *   kind 0 zt pass, 1 apply xy pass, 2..4 CG passes P1/P3/P5, 5..6 reliable-update
  *   passes; real_bytes 4 (FP32 kernels) or 8 (FP64 kernels).
  * Until wz_probe_end, every launch of that class is bracketed by CUDA events
- * on its stream (first 8192 launches) and each block that does work (is not
- * gated off) adds the algorithmic bytes it moves -- the spinor, phi and
- * table bytes it must read and write -- to a device counter.  wz_probe_end
- * synchronises the device and returns the summed event time of the timed
- * launches and the summed algorithmic bytes. */
+ * on its stream (the first 32768 launches) and each block of a timed launch
+ * that does work (is not gated off) adds the algorithmic bytes it moves --
+ * the spinor, phi and table bytes it must read and write -- to a device
+ * counter.  wz_probe_end synchronises the device and returns the summed
+ * event time and the summed algorithmic bytes, both over the timed launches
+ * only, so bytes / total_ms is the achieved rate of those launches. */
 typedef struct wz_probe_result {
   long launches;        /* launches of the class while armed */
   long timed_launches;  /* launches bracketed by events */
   double total_ms;      /* summed event time of the timed launches */
-  double bytes;         /* algorithmic bytes moved by the blocks that ran */
+  double bytes;         /* algorithmic bytes moved by the blocks of the timed launches */
 } wz_probe_result;
 int wz_probe_begin(int kind, int real_bytes);
 int wz_probe_end(wz_probe_result* out);

@@ -156,6 +156,8 @@ def _load():
         "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
         "wz_locality": ([P, ctypes.POINTER(D), I], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
+        "wz_set_workspace_limit": ([P, ctypes.c_size_t], I),
+        "wz_workspace_bytes": ([P], ctypes.c_size_t),
         "wz_selftest_wait_timeout": ([I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)], I),
         "wz_probe_begin": ([I, I], I),
         "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
@@ -176,7 +178,7 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
            "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity", "wz_supercurrent", "wz_one_loop",
            "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end",
-           "wz_selftest_wait_timeout")
+           "wz_selftest_wait_timeout", "wz_set_workspace_limit", "wz_workspace_bytes")
 
 
 def _is_torch(x):
@@ -479,6 +481,12 @@ class Lattice:
 
     def set_phi(self, phi):
         return wz_set_phi(self.ctx, phi)
+
+    def set_workspace_limit(self, nbytes):
+        return check(self.ctx, LIB.wz_set_workspace_limit(self.ctx, int(nbytes)))
+
+    def workspace_bytes(self):
+        return int(LIB.wz_workspace_bytes(self.ctx))
 
     def _nrhs(self, f):
         n = f.numel() if _is_torch(f) else f.size

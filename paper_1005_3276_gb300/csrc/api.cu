@@ -348,6 +348,10 @@ int create_ctx(const wz_params* ps, int nm, void* stream, wz_ctx** out) {
   c->V = (long)T * Z * Y * X;
   c->stream = (cudaStream_t)stream;
   cudaGetDevice(&c->device);
+  for (DevBuf* b : {&c->ws_apply, &c->ws_stage, &c->ws_solver, &c->ws_red, &c->ws_force, &c->ws_rat}) {
+    b->used = &c->ws_used;
+    b->cap = &c->ws_cap;
+  }
   // WZ_NO_GRAPHS=1 in the environment makes the solver launch its chunks
   // eagerly instead of through the cached CUDA graph (same kernels, same results)
   const char* ng = getenv("WZ_NO_GRAPHS");
@@ -448,6 +452,14 @@ int wz_destroy(wz_ctx* c) {
 
 const char* wz_last_error(const wz_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+int wz_set_workspace_limit(wz_ctx* c, size_t bytes) {
+  if (!c) return WZ_EINVAL;
+  c->ws_cap = bytes;
+  return WZ_OK;
+}
+
+size_t wz_workspace_bytes(const wz_ctx* c) { return c ? c->ws_used : 0; }
+
 int wz_set_phi(wz_ctx* c, const void* phi) { return set_member_phi(c, 0, phi); }
 
 int wz_apply(wz_ctx* c, int op, int dtype, const void* in, void* out, int nrhs, double shift) {
@@ -495,7 +507,9 @@ int wz_probe_begin(int kind, int real_bytes) {
   if (kind < PK_ZT || kind > PK_RU_P5 || (real_bytes != 4 && real_bytes != 8)) return WZ_EINVAL;
   if (!p.d_blocks && cudaMalloc(&p.d_blocks, sizeof(unsigned long long)) != cudaSuccess) return WZ_ENOMEM;
   if (p.ev.empty()) {
-    p.ev.resize(2 * 8192);
+    // enough pairs for every launch of a kernel class in one 16^4 x 12 RHS
+    // solve (about 24k zt launches); launches past the pool are not timed
+    p.ev.resize(2 * 32768);
     for (auto& e : p.ev)
       if (cudaEventCreate(&e) != cudaSuccess) return WZ_ECUDA;
   }

@@ -20,6 +20,24 @@ static cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// The dynamic shared-memory attribute is a property of a kernel on one device:
+// a process that drives several devices sets it once on each of them.
+#define WZ_MAX_DEVICES 64
+struct SmemAttrDone {
+  bool done[WZ_MAX_DEVICES] = {};
+};
+template <typename Kern>
+static cudaError_t set_smem_once(Kern k, size_t bytes, SmemAttrDone& d) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= WZ_MAX_DEVICES) return set_smem(k, bytes);  // beyond the table: every launch
+  if (d.done[dev]) return cudaSuccess;
+  e = set_smem(k, bytes);
+  if (e == cudaSuccess) d.done[dev] = true;
+  return e;
+}
+
 template <typename R, int L> cudaError_t launch_xy_L(int mode, const XYArgs<R>& a, cudaStream_t st);
 template <typename R, typename LO, int L>
 cudaError_t launch_cg_L(bool pc, int mode, const CGArgs<R, LO>& a, int nrhs, cudaStream_t st);

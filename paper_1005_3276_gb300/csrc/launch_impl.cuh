@@ -65,11 +65,10 @@ template <typename R, int L, int MODE, bool STAGE>
 static cudaError_t launch_xy_s(const XYArgs<R>& a, int grid, double blk_bytes, cudaStream_t st) {
   using S = XYShape<L>;
   const size_t smem = XYSmem<R, L, MODE, STAGE>::total;
-  static bool attr_done = false;  // one attribute call per instantiation and process
-  if (!attr_done) {
-    cudaError_t e = set_smem(xy_pass<R, L, MODE, STAGE>, smem);
+  static SmemAttrDone attr;  // one attribute call per instantiation and device
+  {
+    cudaError_t e = set_smem_once(xy_pass<R, L, MODE, STAGE>, smem, attr);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   return probed(PK_XY, (int)sizeof(R), blk_bytes, st, [&](unsigned long long* cnt) {
     XYArgs<R> b = a;
@@ -126,11 +125,10 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   constexpr int C = S::C;
   using ZS = ZTSmem<R, NZ, NT, MUL>;
   const size_t smem = ZS::total;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = set_smem(zt_pass<R, NZ, NT, MUL>, smem);
+  static SmemAttrDone attr;
+  {
+    cudaError_t e = set_smem_once(zt_pass<R, NZ, NT, MUL>, smem, attr);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   const long grid = (long)nrhs * a.ntiles;
   if (grid == 0) return cudaSuccess;
@@ -194,11 +192,10 @@ template <typename R, typename LO, int L, int MODE, bool PC>
 static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st) {
   using S = XYShape<L>;
   const size_t smem = CGSmem<R, L, MODE, PC>::total;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaError_t e = set_smem(xy_cg<R, LO, L, MODE, PC>, smem);
+  static SmemAttrDone attr;
+  {
+    cudaError_t e = set_smem_once(xy_cg<R, LO, L, MODE, PC>, smem, attr);
     if (e != cudaSuccess) return e;
-    attr_done = true;
   }
   dim3 grid(a.nblk, nrhs);
   // algorithmic bytes of one block (PPC planes of L x L sites, 4 spins)
@@ -243,15 +240,12 @@ template <int L>
 cudaError_t launch_fk_L(int which, const ForceArgs<double>& a, dim3 grid, cudaStream_t st) {
   using S = XYShape<L>;
   const size_t smem = sizeof(cplx<double>) * S::PLANE * S::PPC + 33 * sizeof(double);
-  static bool done[3] = {false, false, false};
+  static SmemAttrDone done[3];
   cudaError_t e = cudaSuccess;
-  if (!done[which]) {
-    if (which == FK_FORCE) e = set_smem(xy_force<L>, smem);
-    if (which == FK_BOSON_FWD) e = set_smem(xy_boson_fwd<L>, smem);
-    if (which == FK_BOSON_INV) e = set_smem(xy_boson_inv<L>, smem);
-    if (e != cudaSuccess) return e;
-    done[which] = true;
-  }
+  if (which == FK_FORCE) e = set_smem_once(xy_force<L>, smem, done[0]);
+  if (which == FK_BOSON_FWD) e = set_smem_once(xy_boson_fwd<L>, smem, done[1]);
+  if (which == FK_BOSON_INV) e = set_smem_once(xy_boson_inv<L>, smem, done[2]);
+  if (e != cudaSuccess) return e;
   count_launch();
   if (which == FK_FORCE) xy_force<L><<<grid, S::THREADS, smem, st>>>(a);
   if (which == FK_BOSON_FWD) xy_boson_fwd<L><<<grid, S::THREADS, smem, st>>>(a);

@@ -34,21 +34,34 @@ template <typename R> struct Tables {
   void* block = nullptr;  // single allocation holding everything above
 };
 
-// A device buffer that only grows.
+// A device buffer that only grows.  The buffers of one context share a byte
+// count and an optional cap on it (wz_set_workspace_limit): a growth beyond
+// the cap is refused as cudaMalloc refuses one beyond free memory, before the
+// old buffer is released.
 struct DevBuf {
   void* ptr = nullptr;
   size_t bytes = 0;
+  size_t* used = nullptr;       // the context's workspace bytes (may be null)
+  const size_t* cap = nullptr;  // the context's cap, 0 = none (may be null)
   cudaError_t reserve(size_t n) {
     if (n <= bytes) return cudaSuccess;
+    if (used && cap && *cap && *used - bytes + n > *cap) return cudaErrorMemoryAllocation;
     if (ptr) cudaFree(ptr);
+    if (used) *used -= bytes;
     ptr = nullptr;
     bytes = 0;
     cudaError_t e = cudaMalloc(&ptr, n);
-    if (e == cudaSuccess) bytes = n;
+    if (e == cudaSuccess) {
+      bytes = n;
+      if (used) *used += n;
+    } else {
+      cudaGetLastError();  // an allocation failure is not sticky: keep it out of later launch checks
+    }
     return e;
   }
   void release() {
     if (ptr) cudaFree(ptr);
+    if (used) *used -= bytes;
     ptr = nullptr;
     bytes = 0;
   }
@@ -134,6 +147,8 @@ struct wz_ctx {
   wz::DevBuf ws_red;      // reduction partials and per-RHS scalars
   wz::DevBuf ws_force;    // force / HMC fields
   wz::DevBuf ws_rat;      // shifted solutions of a rational apply
+  size_t ws_used = 0;     // bytes held by the six workspaces above
+  size_t ws_cap = 0;      // cap on ws_used (wz_set_workspace_limit), 0 = none
   // small pinned block for scalar read-back: [0, WZ_PINNED_SCRATCH_OFFSET) holds
   // the solver's per-RHS state, the rest is scratch for other reductions
   void* host_pinned = nullptr;

@@ -5,7 +5,9 @@
 // records a CUDA event pair around the launch on the launching stream and
 // hands the kernel a device counter that each block which does work (i.e.
 // is not gated off) increments once.  The algorithmic bytes of the probed
-// launches are then (blocks that ran) x (bytes one block must move).
+// launches are then (blocks that ran) x (bytes one block must move).  The
+// event pool holds a fixed number of pairs; launches beyond it are counted
+// but neither timed nor added to the byte counter.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -44,12 +46,16 @@ inline cudaError_t probed(int kind, int real_bytes, double bytes_per_block, cuda
   if (!on) return launch((unsigned long long*)nullptr);
   const int pair = p.recorded;
   const bool rec = 2 * pair + 1 < (int)p.ev.size();
-  if (rec) cudaEventRecord(p.ev[2 * pair], st);
-  cudaError_t e = launch(p.d_blocks);
-  if (rec) {
-    cudaEventRecord(p.ev[2 * pair + 1], st);
-    p.recorded += 1;
+  // only a launch with an event pair adds its bytes: achieved = bytes / time
+  // then covers the same launches on both sides of the division
+  if (!rec) {
+    p.launches += 1;
+    return launch((unsigned long long*)nullptr);
   }
+  cudaEventRecord(p.ev[2 * pair], st);
+  cudaError_t e = launch(p.d_blocks);
+  cudaEventRecord(p.ev[2 * pair + 1], st);
+  p.recorded += 1;
   p.launches += 1;
   p.bytes_per_block = bytes_per_block;
   return e;

@@ -71,7 +71,9 @@ def test_context_calls_reject_a_null_context(wz):
         "wz_locality": lambda: L.wz_locality(n, n, 0),
         "wz_spectral_bounds": lambda: L.wz_spectral_bounds(n, n, n),
         "wz_apply_mdagm_noalloc": lambda: L.wz_apply_mdagm_noalloc(n, 0, n, n, 1, 0.0),
+        "wz_set_workspace_limit": lambda: L.wz_set_workspace_limit(n, 0),
     }
     for name, call in calls.items():
         assert call() == wz.WZ_EINVAL, name
     assert L.wz_destroy(n) == wz.WZ_OK
+    assert L.wz_workspace_bytes(n) == 0

@@ -2,7 +2,10 @@
 
 A bounded device wait is made to run out on a barrier that nothing completes
 (no copy is issued), and the status comes back as WZ_ETIMEOUT; the device keeps
-working afterwards.
+working afterwards.  An out-of-memory workspace growth is made on the host: a
+workspace cap below what a solve needs refuses the growth the way cudaMalloc
+refuses one beyond free memory, the call returns WZ_ENOMEM, and the same
+context then solves once the cap is lifted.
 """
 
 import numpy as np
@@ -39,4 +42,35 @@ def test_bounded_wait_runs_out_with_status(wz):
     x = np.zeros((2,) + dims + (4,), np.complex128)
     rc, st, _ = lat.solve(synth.spinor_rhs(2, dims, 2), x, tol=1e-10)
     assert rc == wz.WZ_OK and st["converged"] == 2
+    lat.close()
+
+
+def test_workspace_growth_refused_with_enomem(wz):
+    from oracle import cg as ocg
+    import oracle
+    dims = (8, 8, 8, 8)
+    P = oracle.Params(dims=dims, m=0.2, g=0.5)
+    phi = synth.scalar_field(dims, 0.5, 3)
+    b = torch.from_numpy(synth.spinor_rhs(4, dims, 4)).cuda()
+    x = torch.zeros_like(b)
+    lat = wz.Lattice(dims, m=P.m, g=P.g)
+    lat.set_phi(phi)
+    # one right-hand side fits and leaves workspace behind
+    lat.solve(b[:1].contiguous(), x[:1].contiguous(), tol=1e-10)
+    held = lat.workspace_bytes()
+    assert held > 0
+    lat.set_workspace_limit(held)  # exactly what it holds: no room to grow
+    with pytest.raises(wz.WzError) as e:
+        lat.solve(b, x, tol=1e-10)
+    assert e.value.code == wz.WZ_ENOMEM
+    assert lat.workspace_bytes() == held  # the refused growth released nothing
+    # a call that fits the existing workspace still runs under the cap
+    x1 = torch.zeros_like(b[:1])
+    rc, st, _ = lat.solve(b[:1].contiguous(), x1, tol=1e-10)
+    assert rc == wz.WZ_OK
+    lat.set_workspace_limit(0)
+    rc, st, _ = lat.solve(b, x, tol=1e-10)
+    assert rc == wz.WZ_OK and st["converged"] == 4
+    xb, bb = x.cpu().numpy(), b.cpu().numpy()
+    assert max(ocg.true_residual(P, phi, bb[k], xb[k]) for k in range(4)) <= 1e-10
     lat.close()

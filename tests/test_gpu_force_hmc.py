@@ -131,6 +131,45 @@ def test_trajectory_matches_oracle_4(wz):
     assert st["force_evals"] == 11
 
 
+def test_omelyan_trajectory_matches_oracle_4(wz):
+    """One 4^4 Omelyan 2MN trajectory (lambda = 0.1931833275037836, tau = 1, 4
+    steps) with two pseudofermions and complex couplings, from the device
+    Philox draws reproduced by the oracle's Philox: same dH, decision and phi.
+    The device merges the closing lambda-kick of a step with the opening one of
+    the next (same phi, so the same force): 1 + 2 n force evaluations against
+    the oracle's 3 n, with the same trajectory."""
+    dims = (4, 4, 4, 4)
+    P = oracle.Params(dims=dims, m=0.3 + 0.1j, g=0.6 - 0.2j)
+    phi0 = synth.scalar_field(dims, 0.5, 5)
+    seed, traj, nsteps = 4321, 2, 4
+    lat = wz.Lattice(dims, m=P.m, g=P.g)
+    lat.set_phi(phi0)
+    st = lat.trajectory(tau=1.0, nsteps=nsteps, npf=2, integrator="omelyan", tol=1e-12, seed=seed,
+                        traj_index=traj, flags=wz.WZ_HMC_FP64_SOLVES)
+    phi_gpu = np.zeros_like(phi0)
+    lat.get_phi(phi_gpu)
+    pi0 = philox.momentum_field(seed, traj, dims)
+    R = philox.pseudofermion_source(seed, traj, dims, 2)
+    u = philox.accept_uniform(seed, traj)
+    ref = ohmc.trajectory(P, phi0, pi0, R, u, tau=1.0, nsteps=nsteps, integrator="omelyan", tol=1e-13)
+    print("omelyan 4^4 dH device", st["dH"], "oracle", ref["dH"])
+    assert abs(st["dH"] - ref["dH"]) <= 1e-8 * max(1.0, abs(ref["dH"]))
+    assert abs(st["H0"] - ref["H0"]) <= 1e-10 * abs(ref["H0"])
+    assert bool(st["accept"]) == ref["accept"]
+    assert rel(phi_gpu, ref["phi"]) <= 1e-9
+    # the end of the molecular dynamics as well, whatever the decision
+    lat.set_phi(phi0)
+    pi = torch.from_numpy(pi0.copy()).cuda()
+    etas = torch.from_numpy(np.stack(ref["etas"])).cuda()
+    lat.md_integrate(pi, etas, tau=1.0, nsteps=nsteps, integrator="omelyan", tol=1e-12,
+                      flags=wz.WZ_HMC_FP64_SOLVES)
+    phi_md = torch.zeros_like(pi)
+    lat.get_phi(phi_md)
+    assert rel(phi_md.cpu().numpy(), ref["phi_md"]) <= 1e-9
+    assert rel(pi.cpu().numpy(), ref["pi_md"]) <= 1e-9
+    assert st["force_evals"] == 1 + 2 * nsteps
+
+
 def test_ten_trajectories_4(wz):
     w = synth.SMALL_4
     lat = wz.Lattice(w.dims, m=w.m, g=w.g)

@@ -3,10 +3,11 @@
 wz_apply_mdagm_noalloc is for callers that cannot allocate device memory when
 they apply the operator; it keeps the pass intermediates in a fixed device
 array instead of the context workspace.  Two calls in a row (different
-inputs, both precisions) must give what wz_apply gives, within the apply
-tolerances used everywhere else (1e-12 FP64, 2e-6 FP32 relative); requests
-larger than the array must be refused with a message.  This file is collected
-last so that a stop-at-first-failure run has run every other test first.
+inputs, both precisions) and one in place must give what wz_apply gives,
+within the apply tolerances used everywhere else (1e-12 FP64, 2e-6 FP32
+relative); requests larger than the array must be refused with a message.
+This file is collected last so that a stop-at-first-failure run has run every
+other test first.
 """
 
 import numpy as np
@@ -48,6 +49,14 @@ def test_noalloc_matches_apply_two_calls(wz, dtype):
         wz.wz_apply_mdagm_noalloc(lat.ctx, x, y, 2, shift)
         torch.cuda.synchronize()
         assert rel(y, y_ref) <= TOL[dtype], f"call {call}"
+    # in place (input and output the same field), with a shift: the shift term
+    # reads the input last, after the passes have written the output elsewhere
+    y_ref = torch.empty_like(x)
+    lat.apply("MdagM", x, y_ref, 2, 0.25)
+    y = x.clone()
+    wz.wz_apply_mdagm_noalloc(lat.ctx, y, y, 2, 0.25)
+    torch.cuda.synchronize()
+    assert rel(y, y_ref) <= TOL[dtype], "in place"
 
 
 def test_noalloc_rejects_oversize(wz):

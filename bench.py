@@ -39,6 +39,23 @@ sys.path.insert(0, ROOT)
 from paper_1005_3276_gb300 import synth  # noqa: E402
 
 METRIC = "M^dag M applies/s and HMC traj/s at 16^4, mixed vs FP64 GPU @1e-10 residual"
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+PEAK_HBM = measured_peaks().get("hbm_gbs")
+
+
+def mdagm_flops_per_site(V):
+    """Algorithmic flops of one M^dag M apply per site: two M applies, each two
+    4D FFTs of 4 spin components at the paper's 5 N log2 N convention plus ~96
+    flops of site terms (the survey's count: 1472 at V = 16^4)."""
+    return 2.0 * (2.0 * 4.0 * 5.0 * np.log2(V) + 96.0)
 UNIT = "M^dag M applies/s"
 
 
@@ -55,14 +72,18 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory timing")
-    ap.add_argument("--hmc-traj", type=int, default=2, help="timed trajectories per precision")
+    ap.add_argument("--hmc-traj", type=int, default=2, help="timed mixed trajectories (FP64: half, batched: 1)")
+    ap.add_argument("--hmc-replicas", type=int, default=8, help="independent 16^4 replicas of the batched HMC")
+    ap.add_argument("--hmc-therm", type=int, default=4, help="thermalisation trajectories of the HMC start")
     ap.add_argument("--no-sweep", action="store_true", help="skip the L = 8, 16, 32 apply sweep")
-    ap.add_argument("--batch", action="store_true", help="also time the 64-lattice batched workload")
+    ap.add_argument("--no-solve32", action="store_true", help="skip the 32^4 x 4 RHS mixed solve")
+    ap.add_argument("--no-invtab", action="store_true", help="skip the solver-table shaped L^3 x 32 solves")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 64-lattice batched workload")
     ap.add_argument("--no-rhmc", action="store_true", help="skip the rational heatbath / RHMC timings")
     ap.add_argument("--no-oneloop", action="store_true", help="skip the one-loop lattice sums (Sec. 5 tables)")
-    ap.add_argument("--large", action="store_true",
-                    help="also time the 32^4 large-lattice pieces (force evaluation, Ward identity, <F>, "
-                         "supercurrent correlators)")
+    ap.add_argument("--no-large", action="store_true", help="skip the 32^4 Omelyan trajectory and measurements")
+    ap.add_argument("--large-steps", type=int, default=2,
+                    help="Omelyan steps of the 32^4 trajectory at eps = 1/40 (40: the whole trajectory)")
     ap.add_argument("--rhmc-fp64", action="store_true", help="also time the RHMC trajectory with FP64 solves")
     return ap.parse_args()
 
@@ -302,6 +323,10 @@ def main():
     for _ in range(args.warmup):
         solve()
     torch.cuda.synchronize()
+    # FMA throughput of this GPU (the project's microkernel): the ALU roofline
+    # of the FP64 passes
+    fp64_peak, _ = wz.wz_fma_peak(8, 20000)
+    fp32_peak, _ = wz.wz_fma_peak(4, 1000000)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -350,43 +375,94 @@ def main():
         e1.record(stream)
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
+        tf64 = n64 * mdagm_flops_per_site(int(np.prod(w.dims))) * int(np.prod(w.dims)) / (ms64 / 1000.0) / 1e12
         fp64 = {"value": n64 / (ms64 / 1000.0), "unit": UNIT, "ms_per_solve": ms64,
+                "alu_TFLOP_s": tf64, "fp64_fma_peak_TFLOP_s": fp64_peak, "frac_of_fp64_peak": tf64 / fp64_peak,
+                "roofline_note": "FP64 passes are arithmetic-bound on this GPU: M^dag M flops at the paper's "
+                                 "5 N log2 N FFT convention (1472 per site at 16^4) against the measured FP64 "
+                                 "FMA throughput",
                 "iterations": st64["iterations"], "max_true_residual": st64["max_true_residual"],
                 "mixed_speedup_per_solve": ms64 / (total_ms / args.steps)}
 
     # HMC trajectories/s on the differentiation workload (16^4, m = 0.1, g = 0.5,
-    # one pseudofermion, tau = 1, 20 leapfrog steps), mixed and FP64 solves
+    # one pseudofermion, tau = 1, 20 leapfrog steps, CG to 1e-10), mixed and
+    # FP64 solves, one lattice and a batch of R independent replicas (one
+    # context, the replicas as members; each trajectory of the batch is one
+    # CUDA graph).  All start from the same configurations, thermalised by
+    # args.hmc_therm shorter trajectories (tau 0.5, 10 steps) of the batch.
     hmc = None
     if not args.no_hmc:
         hw = synth.FORCE_16
-        hlat = wz.Lattice(hw.dims, m=hw.m, g=hw.g, stream=stream.cuda_stream)
-        hmc = {"workload": f"{hw.name}: 16^4, m={hw.m}, g={hw.g}, phi sigma {hw.sigma}, 1 pseudofermion, "
-                           f"tau={hw.extra['tau']}, {hw.extra['nsteps']} leapfrog steps, CG to 1e-10"}
-        for label, flags in (("mixed", 0), ("fp64", wz.WZ_HMC_FP64_SOLVES)):
-            hlat.set_phi(torch.from_numpy(synth.scalar_field(hw.dims, hw.sigma, 0)).cuda())
-            kw = dict(tau=hw.extra["tau"], nsteps=hw.extra["nsteps"], npf=1, tol=1e-10, seed=2024, flags=flags)
-            hlat.trajectory(traj_index=0, **kw)  # warm-up
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            sts = []
-            e0.record(stream)
-            for t in range(args.hmc_traj):
-                sts.append(hlat.trajectory(traj_index=1 + t, **kw))
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1)
-            hmc[label] = {"traj_per_s": args.hmc_traj / (ms / 1000.0), "ms_per_traj": ms / args.hmc_traj,
-                          "cg_iterations_per_traj": float(np.mean([x["cg_iterations"] for x in sts])),
-                          "dH": [round(x["dH"], 5) for x in sts], "accept": [x["accept"] for x in sts]}
-        hmc["mixed_speedup"] = hmc["fp64"]["ms_per_traj"] / hmc["mixed"]["ms_per_traj"]
-        # the CG iterations of a trajectory as a whole-iteration HBM figure: one
-        # FP32 (FP64) iteration moves 18 spinor fields and phi twice per site
         V = int(np.prod(hw.dims))
-        for label, bps in (("mixed", 18 * 32 + 2 * 8), ("fp64", 18 * 64 + 2 * 16)):
-            h = hmc[label]
-            h["cg_bytes_per_site_iteration"] = bps
-            h["cg_GB_s"] = h["cg_iterations_per_traj"] * bps * V / (h["ms_per_traj"] / 1000.0) / 1e9
+        R = args.hmc_replicas
+        kw = dict(tau=hw.extra["tau"], nsteps=hw.extra["nsteps"], npf=1, tol=1e-10)
+        hmc = {"workload": f"{hw.name}: 16^4, m={hw.m}, g={hw.g}, 1 pseudofermion, tau={hw.extra['tau']}, "
+                           f"{hw.extra['nsteps']} leapfrog steps, CG to 1e-10; start: {R} configurations drawn "
+                           f"with sigma {hw.sigma}, then {args.hmc_therm} trajectories of tau 0.5, 10 steps",
+               "bytes_per_site_cg_iteration": {"mixed": 18 * 32 + 2 * 8, "fp64": 18 * 64 + 2 * 16},
+               "bytes_per_site_mdagm": {"mixed": 440, "fp64": 880}}
+        bt = wz.Batch([dict(dims=hw.dims, m=hw.m, g=hw.g)] * R)
+        for i in range(R):
+            bt.set_phi(i, torch.from_numpy(synth.scalar_field(hw.dims, hw.sigma, 300 + i)).cuda())
+        therm = []
+        for t in range(args.hmc_therm):
+            sts = bt.trajectory(tau=0.5, nsteps=10, npf=1, tol=1e-10, seed=555, traj_index=t)
+            therm.append([round(x["dH"], 3) for x in sts])
+        hmc["thermalisation_dH"] = therm
+        phis = []
+        for i in range(R):
+            p = torch.zeros(hw.dims, dtype=torch.complex128, device="cuda")
+            bt.get_phi(i, p)
+            phis.append(p)
+
+        def fractions(d, label, ms, iters):
+            d["cg_GB_s"] = iters * hmc["bytes_per_site_cg_iteration"][label] * V / (ms / 1000.0) / 1e9
+            d["cg_frac_of_hbm"] = d["cg_GB_s"] / (PEAK_HBM or 6800.0)
+            d["mdagm_frac_of_hbm"] = (iters * hmc["bytes_per_site_mdagm"][label] * V / (ms / 1000.0) / 1e9
+                                      / (PEAK_HBM or 6800.0))
+
+        hlat = wz.Lattice(hw.dims, m=hw.m, g=hw.g, stream=stream.cuda_stream)
+        for label, flags in (("mixed", 0), ("fp64", wz.WZ_HMC_FP64_SOLVES)):
+            n = args.hmc_traj if label == "mixed" else max(1, args.hmc_traj // 2)
+            hlat.set_phi(phis[0])
+            hlat.trajectory(traj_index=1000, seed=2024, flags=flags, **kw)  # warm-up (graph capture)
+            hlat.set_phi(phis[0])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sts = [hlat.trajectory(traj_index=t, seed=2024, flags=flags, **kw) for t in range(n)]
+            torch.cuda.synchronize()
+            ms = 1000.0 * (time.perf_counter() - t0)
+            iters = float(sum(x["cg_iterations"] for x in sts))
+            d = {"traj_per_s": n / (ms / 1000.0), "ms_per_traj": ms / n, "trajectories": n,
+                 "cg_iterations_per_traj": iters / n, "dH": [round(x["dH"], 4) for x in sts],
+                 "accepted": int(sum(x["accept"] for x in sts))}
+            fractions(d, label, ms, iters)
+            hmc["single_" + label] = d
         hlat.close()
+        for label, flags in (("mixed", 0), ("fp64", wz.WZ_HMC_FP64_SOLVES)):
+            n = args.hmc_traj if label == "mixed" else 1
+            for i in range(R):
+                bt.set_phi(i, phis[i])
+            bt.trajectory(traj_index=1000, seed=2024, flags=flags, **kw)  # warm-up (graph capture)
+            for i in range(R):
+                bt.set_phi(i, phis[i])
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sts = [bt.trajectory(traj_index=t, seed=2024, flags=flags, **kw) for t in range(n)]
+            torch.cuda.synchronize()
+            ms = 1000.0 * (time.perf_counter() - t0)
+            iters = float(sum(x[0]["cg_iterations"] for x in sts))  # all members of the group together
+            d = {"replicas": R, "traj_per_s": R * n / (ms / 1000.0), "ms_per_batch_traj": ms / n,
+                 "trajectories_per_replica": n, "cg_iterations_per_batch_traj": iters / n,
+                 "dH": [[round(x["dH"], 4) for x in st] for st in sts],
+                 "accepted": int(sum(x["accept"] for st in sts for x in st)), "of": R * n}
+            fractions(d, label, ms, iters)
+            hmc[f"batch{R}_" + label] = d
+        bt.close()
+        hmc["batched_mixed_over_single_fp64"] = hmc[f"batch{R}_mixed"]["traj_per_s"] / hmc["single_fp64"]["traj_per_s"]
+        hmc["batched_mixed_over_batched_fp64"] = (hmc[f"batch{R}_mixed"]["traj_per_s"]
+                                                  / hmc[f"batch{R}_fp64"]["traj_per_s"])
+        hmc["single_mixed_over_single_fp64"] = hmc["single_mixed"]["traj_per_s"] / hmc["single_fp64"]["traj_per_s"]
 
     # rational heatbath eta = (M^dag M)^1/8 R of the paper's heatbath table: L^3 x 32,
     # m = 1, g = 0.1, degree 20, poles beta <= 100 preconditioned by M0^-1; the
@@ -447,6 +523,39 @@ def main():
                                          "accept": [x["accept"] for x in sts]}
         tl.close()
 
+    # CG solves shaped like the paper's solver table (Sec. 7.4): L^3 x 32, m = 1,
+    # g = 0.2, one Gaussian right-hand side; unpreconditioned and M0^-1
+    # preconditioned; FP32 iteration to 1e-6 and FP64 to 1e-12 (true residual).
+    # Printed beside the paper's GTX 285 seconds and iterations (context only).
+    invtab = None
+    if not args.no_invtab:
+        paper = {"8^3x32": {"single": (1.3, 830, 0.038, 8), "double": (4.9, 1600, 0.13, 15)},
+                 "16^3x32": {"single": (7.1, 870, 0.20, 8), "double": (31, 1800, 0.74, 15)}}
+        invtab = {"workload": "L^3 x 32, m = 1, g = 0.2, phi sigma 0.5, 1 complex-Gaussian RHS; "
+                              "'single' = FP32 iteration with FP64 reliable updates to 1e-6, "
+                              "'double' = FP64 to 1e-12 (true residuals)", "rows": []}
+        for L in (8, 16):
+            dims = (32, L, L, L)
+            il = wz.Lattice(dims, m=1.0, g=0.2, stream=stream.cuda_stream)
+            il.set_phi(torch.from_numpy(synth.scalar_field(dims, 0.5, 0)).cuda())
+            bi = torch.from_numpy(synth.spinor_rhs(1, dims, 1)).cuda()
+            xi = torch.zeros_like(bi)
+            row = {"lattice": f"{L}^3x32", "paper_gtx285": paper[f"{L}^3x32"]}
+            for prec, mixed, tol in (("single", True, 1e-6), ("double", False, 1e-12)):
+                for pc in (False, True):
+                    il.solve(bi, xi, tol=tol, mixed=mixed, pc=pc)  # warm-up (graph, tuner)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    rc, st, _ = il.solve(bi, xi, tol=tol, mixed=mixed, pc=pc)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    row[f"{prec}_{'pc' if pc else 'npc'}"] = {
+                        "seconds": e0.elapsed_time(e1) / 1000.0, "iterations": st["iterations"],
+                        "reliable_updates": st["reliable_updates"], "true_residual": st["max_true_residual"]}
+            invtab["rows"].append(row)
+            il.close()
+
     # one-loop counterterms of Tables sse, fse, ase at mL = 8 (N = 8 / ma up to 1024),
     # FP64 on the device, beside the paper's printed mL = 8 columns
     oneloop = None
@@ -466,84 +575,146 @@ def main():
                                     "paper_mL8": ref, "seconds": dt,
                                     "terms_per_s": N ** 4 / 48.0 / dt})
 
-    # large single lattice: 32^4, m = 0.02, g = 1.0, hot start sigma 1, 4 pseudofermions.
-    # A whole trajectory (Omelyan, 40 steps = 81 force evaluations) is minutes; the
-    # pieces of one are timed: a force evaluation with its 4-RHS mixed solve, the
-    # Ward-identity measurement (4 uniform-source solves), <F> and the supercurrent
-    # correlators on a Gaussian noise source (4 solves).
+    # large single lattice: 32^4, m = 0.02, g = 1.0, hot start sigma 1, 4
+    # pseudofermions, mixed CG to 1e-10.  One Omelyan 2MN trajectory at the
+    # workload's step size eps = tau / 40 = 0.025, over args.large_steps steps
+    # (40 = the whole trajectory of length 1; the default 2 steps is a
+    # trajectory of length 0.05 at the same step size), then the measurements
+    # of the new configuration: <F~>, both sides of the Ward identity and the
+    # supercurrent correlators on one Gaussian noise source.
     large = None
-    if args.large:
+    if not args.no_large:
         lw = synth.LARGE_32
         ll = wz.Lattice(lw.dims, m=lw.m, g=lw.g, stream=stream.cuda_stream)
         ll.set_phi(torch.from_numpy(synth.scalar_field(lw.dims, lw.sigma, 0)).cuda())
-        eta = torch.from_numpy(synth.spinor_rhs(lw.nrhs, lw.dims, 1)).cuda()
-        G = torch.zeros(lw.dims, dtype=torch.complex128, device="cuda")
+        nst = args.large_steps
+        eps = lw.extra["tau"] / lw.extra["nsteps"]
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        sb, spf, fst = ll.force(eta, G, tol=1e-10)
+        tst = ll.trajectory(tau=eps * nst, nsteps=nst, npf=lw.nrhs, integrator="omelyan", tol=1e-10, seed=9,
+                            traj_index=0)
         torch.cuda.synchronize()
-        t_force = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        WR, WL, wst = ll.ward_identity(tol=1e-10, mixed=True)
-        t_ward = time.perf_counter() - t0
+        t_traj = time.perf_counter() - t0
         t0 = time.perf_counter()
         F = ll.aux_vev()
         t_aux = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        WR, WL, wst = ll.ward_identity(tol=1e-10, mixed=True)
+        t_ward = time.perf_counter() - t0
         # supercurrent correlators on one Gaussian noise source, E[w w^*] = 1 per site
         wsrc = torch.from_numpy(synth.scalar_field(lw.dims, np.sqrt(0.5), 2)).cuda()
         t0 = time.perf_counter()
         Rsc, sst = ll.supercurrent(wsrc, tol=1e-10, mixed=True)
         t_sc = time.perf_counter() - t0
-        large = {"workload": f"{lw.name}: 32^4, m={lw.m}, g={lw.g}, phi sigma {lw.sigma}, {lw.nrhs} pseudofermions, "
-                             "mixed CG to 1e-10",
-                 "force_eval_s": t_force, "force_cg_iterations_max": fst["iterations"],
-                 "force_cg_iterations_total": fst["total_iterations"],
+        V32 = int(np.prod(lw.dims))
+        gbs = tst["cg_iterations"] * 592.0 * V32 / t_traj / 1e9
+        large = {"workload": f"{lw.name}: 32^4, m={lw.m}, g={lw.g}, hot start phi sigma {lw.sigma}, {lw.nrhs} "
+                             f"pseudofermions, Omelyan 2MN at eps = {eps:g}, mixed CG to 1e-10",
+                 "md_steps": nst, "tau": eps * nst, "full_trajectory": nst == lw.extra["nsteps"],
+                 "trajectory_s": t_traj, "force_evals": tst["force_evals"], "cg_iterations": tst["cg_iterations"],
+                 "dH": tst["dH"], "accept": tst["accept"],
+                 "cg_GB_s": gbs, "cg_frac_of_hbm": gbs / (PEAK_HBM or 6800.0),
+                 "est_full_trajectory_s": t_traj * (2 * lw.extra["nsteps"] + 1) / max(1, tst["force_evals"]),
+                 "aux_vev": [F.real, F.imag], "aux_s": t_aux,
                  "ward_s": t_ward, "ward_cg_iterations_max": wst["iterations"],
                  "ward_R_trace": [float(np.trace(WR).real), float(np.trace(WR).imag)],
-                 "ward_L_00_01": [float(WL[0, 1].real), float(WL[0, 1].imag)],
-                 "aux_vev": [F.real, F.imag], "aux_s": t_aux,
+                 "ward_L_trace": [float(np.trace(WL).real), float(np.trace(WL).imag)],
                  "supercurrent_s": t_sc, "supercurrent_cg_iterations_max": sst["iterations"],
                  "supercurrent_R0_mu0_dx1_dy0_trace": [float(np.trace(Rsc[0, 0, 1, 0]).real),
                                                        float(np.trace(Rsc[0, 0, 1, 0]).imag)]}
         ll.close()
 
-    # apply-throughput sweep: (M^dag M) on L^4, FP32 vs FP64 fields, about 1M
-    # site-RHS per launch sequence (256 / 16 / 1 right-hand sides at L = 8/16/32)
+    # apply-throughput sweep: (M^dag M) on L^4, FP32 vs FP64 fields.  Every
+    # repetition starts from a flushed L2 (256 MB write, outside its events),
+    # so inputs and outputs come from HBM; the pass intermediates of one apply
+    # stay wherever the hardware keeps them.  The zt and xy passes of the FP32
+    # apply are then probed one launch at a time (CUDA events per launch).
     sweep = None
     if not args.no_sweep:
         sweep = []
-        for L in (8, 16, 32):
+        for L, nr in ((8, 256), (16, 16), (16, 3), (32, 1), (32, 4)):
             dims = (L, L, L, L)
-            nr = max(1, (1 << 20) // (L ** 4))
             slat = wz.Lattice(dims, m=w.m, g=w.g, stream=stream.cuda_stream)
             slat.set_phi(torch.from_numpy(synth.scalar_field(dims, w.sigma, 0)).cuda())
             row = {"L": L, "nrhs": nr}
             for name, dt, S in (("fp32", torch.complex64, 32), ("fp64", torch.complex128, 64)):
+                if name == "fp64" and nr == 3:
+                    continue
                 x = torch.from_numpy(synth.spinor_rhs(nr, dims, 1)).to(dt).cuda()
                 y = torch.empty_like(x)
                 for _ in range(3):
                     slat.apply("MdagM", x, y, nr)
                 reps = 10
-                flush.zero_()
-                torch.cuda.synchronize()
-                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
+                times = []
                 for _ in range(reps):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
                     slat.apply("MdagM", x, y, nr)
-                e1.record(stream)
-                torch.cuda.synchronize()
-                ms = e0.elapsed_time(e1) / reps
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = float(np.median(times))
                 # five passes: 13 spinor fields + 2 phi per site-RHS
                 gbs = (13 * S + 2 * S // 4) * L ** 4 * nr / (ms / 1000.0) / 1e9
-                row[name] = {"applies_per_s": nr / (ms / 1000.0), "ms": ms, "GB_s": gbs}
-            row["fp32_over_fp64"] = row["fp32"]["applies_per_s"] / row["fp64"]["applies_per_s"]
+                row[name] = {"applies_per_s": nr / (ms / 1000.0), "ms": ms, "GB_s": gbs,
+                             "frac_of_hbm": gbs / (PEAK_HBM or 6800.0)}
+                tf = mdagm_flops_per_site(L ** 4) * L ** 4 * nr / (ms / 1000.0) / 1e12
+                row[name]["alu_TFLOP_s"] = tf
+                row[name]["frac_of_fma_peak"] = tf / (fp64_peak if name == "fp64" else fp32_peak)
+                if name == "fp32":
+                    kk = {}
+                    for kind in ("zt", "xy"):
+                        flush.zero_()
+                        torch.cuda.synchronize()
+                        wz.wz_probe_begin(kind, 4)
+                        slat.apply("MdagM", x, y, nr)
+                        kk[kind] = wz.wz_probe_end()
+                    for kind, v in kernel_table(kk).items():
+                        row[name][kind + "_per_launch"] = {
+                            "launches": v["launches"], "avg_launch_us": v["avg_launch_us"],
+                            "algorithmic_bytes_per_launch": v["algorithmic_bytes_per_launch"],
+                            "GB_s": v["achieved_GB_s"],
+                            "frac_of_hbm": v["achieved_GB_s"] / (PEAK_HBM or 6800.0) if v["achieved_GB_s"] else None}
+            if "fp64" in row:
+                row["fp32_over_fp64"] = row["fp32"]["applies_per_s"] / row["fp64"]["applies_per_s"]
             sweep.append(row)
             slat.close()
+
+    # the mixed solve on a lattice whose working set is far beyond L2: 32^4,
+    # 4 right-hand sides (5 FP32 fields of 128 MB plus the FP64 vectors), the
+    # same couplings and tolerance as the 16^4 headline
+    solve32 = None
+    if not args.no_solve32:
+        dims = (32, 32, 32, 32)
+        l32 = wz.Lattice(dims, m=w.m, g=w.g, stream=stream.cuda_stream)
+        l32.set_phi(torch.from_numpy(synth.scalar_field(dims, w.sigma, 0)).cuda())
+        b32 = torch.from_numpy(synth.spinor_rhs(4, dims, 1)).cuda()
+        x32 = torch.zeros_like(b32)
+        l32.solve(b32, x32, tol=w.tol, mixed=True)  # warm-up: tuner and graph
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc, st32, _ = l32.solve(b32, x32, tol=w.tol, mixed=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        n32 = st32["total_iterations"] + st32["reliable_updates"]
+        gbs = n32 * 592.0 * 32 ** 4 / (ms / 1000.0) / 1e9
+        solve32 = {"workload": f"32^4, m={w.m}, g={w.g}, phi sigma {w.sigma}, 4 complex-Gaussian RHS, mixed CG to "
+                               f"{w.tol:g}", "ms_per_solve": ms, "applies_per_s": n32 / (ms / 1000.0),
+                   "iterations_max": st32["iterations"], "max_true_residual": st32["max_true_residual"],
+                   "cg_GB_s": gbs, "cg_frac_of_hbm": gbs / (PEAK_HBM or 6800.0),
+                   "note": "592 B per site-RHS per CG iteration (18 FP32 spinor fields + 2 phi); working set "
+                           "~0.9 GB, far beyond the 129 MB L2"}
+        l32.close()
 
     # batched workload: 64 lattices (16 each of 4^4, 8^4, 12^4, 16^4), (m, g)
     # on an 8 x 8 grid, 8 right-hand sides each, one mixed solve to 1e-10
     batch = None
-    if args.batch:
+    if not args.no_batch:
         ws = synth.batch_workloads()
         bt = wz.Batch([dict(dims=x.dims, m=x.m, g=x.g) for x in ws])
         bs, xs = [], []
@@ -559,10 +730,13 @@ def main():
         dt = time.perf_counter() - t0
         applies = bst["total_iterations"] + bst["reliable_updates"]
         site_rhs = sum(int(np.prod(x.dims)) * x.nrhs for x in ws)
+        gbs = bst["site_applies"] * 592.0 / dt / 1e9
         batch = {"workload": "64 lattices: 16 each of 4^4, 8^4, 12^4, 16^4; m in linspace(0.02, 0.2, 8), "
                              "g in linspace(0.1, 1.0, 8); 8 RHS each; mixed CG to 1e-10",
                  "groups": bt.groups, "seconds": dt, "applies": applies, "applies_per_s": applies / dt,
-                 "site_rhs_applies_per_s": None, "max_iterations": bst["iterations"],
+                 "site_rhs_applies_per_s": bst["site_applies"] / dt,
+                 "cg_GB_s": gbs, "cg_frac_of_hbm": gbs / (PEAK_HBM or 6800.0),
+                 "max_iterations": bst["iterations"],
                  "max_true_residual": bst["max_true_residual"], "site_rhs": site_rhs}
         t0 = time.perf_counter()
         tst = bt.trajectory(tau=0.1, nsteps=2, npf=8, tol=1e-10, seed=7, traj_index=0)
@@ -586,12 +760,7 @@ def main():
     e2e = {"value": e2e_n / e2e_t if e2e_t > 0 else None, "unit": UNIT, "h2d_bytes_per_step": int(hb.numel() * hb.element_size()),
            "d2h_bytes_per_step": int(hx.numel() * hx.element_size())}
 
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    peak = peaks.get("hbm_gbs")
+    peak = PEAK_HBM
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     kernels = kernel_table(probes)
@@ -629,12 +798,17 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "large": large, "apply_sweep": sweep, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "large": large, "apply_sweep": sweep, "solve_32x4": solve32, "paper_solver_table": invtab,
+            "fma_peak_TFLOP_s": {"fp64": fp64_peak, "fp32": fp32_peak}, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
             "hmc_traj_per_s": None if hmc is None else {
-                "mixed": hmc["mixed"]["traj_per_s"], "fp64": hmc["fp64"]["traj_per_s"],
-                "mixed_over_fp64": hmc["mixed_speedup"],
-                "mixed_cg_frac_of_hbm": hmc["mixed"]["cg_GB_s"] / peak, "workload": hmc["workload"]},
+                "single_mixed": hmc["single_mixed"]["traj_per_s"], "single_fp64": hmc["single_fp64"]["traj_per_s"],
+                f"batch{args.hmc_replicas}_mixed": hmc[f"batch{args.hmc_replicas}_mixed"]["traj_per_s"],
+                f"batch{args.hmc_replicas}_fp64": hmc[f"batch{args.hmc_replicas}_fp64"]["traj_per_s"],
+                "batched_mixed_over_single_fp64": hmc["batched_mixed_over_single_fp64"],
+                "batched_mixed_cg_frac_of_hbm": hmc[f"batch{args.hmc_replicas}_mixed"]["cg_frac_of_hbm"],
+                "single_mixed_cg_frac_of_hbm": hmc["single_mixed"]["cg_frac_of_hbm"],
+                "workload": hmc["workload"]},
         }))
     lat.close()
     if dist is not None:

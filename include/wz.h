@@ -71,8 +71,11 @@ enum wz_op {
   WZ_OP_MTILDE = 6,       /* M~ psi = M M0^-1 psi                   (Eq. theprob) */
   WZ_OP_MTILDE_DAG = 7,   /* M~^dagger psi                                        */
   WZ_OP_MTILDE_DAGM = 8,  /* (M~^dagger M~ + shift) psi                           */
-  WZ_OP_D1 = 9            /* D1 psi: gamma-odd part of the overlap, i gamma.sin p / omega
+  WZ_OP_D1 = 9,           /* D1 psi: gamma-odd part of the overlap, i gamma.sin p / omega
                              in momentum space (Sec. 2.2; the D1 of Eqs. uity, nzav) */
+  WZ_OP_D = 10            /* D psi: the overlap operator D = 1 - V = D1 + D2, with
+                             D2(p) = 1 - b(p)/omega(p) (Sec. 2.2, Eq. d1mom); used by the
+                             locality probe of Sec. 3.2 */
 };
 
 /* Lattice and action parameters (Sec. 2.2, Eq. fmat, Eq. acws). */
@@ -134,6 +137,9 @@ typedef struct wz_solve_stats {
   double max_true_residual;/* max over RHS of ||b - (M^dag M + shift) x|| / ||b||, FP64,
                               of the ORIGINAL (unpreconditioned) system */
   double seconds;          /* host wall time of the call, including the final sync */
+  double site_applies;     /* sum over systems of (inner iterations + reliable updates)
+                              x sites of the system's lattice: the M^dag M work in site
+                              units, comparable across lattices of different size */
 } wz_solve_stats;
 
 /* Solve (M^dagger M + shift) x = b for nrhs independent complex128 fields by
@@ -332,6 +338,11 @@ int wz_supercurrent(wz_ctx* ctx, const void* w, double tol, int maxiter, unsigne
  * at taxi-driver distance r = sum_mu min(|x_mu|, L_mu - |x_mu|).  f needs
  * T/2 + Z/2 + Y/2 + X/2 + 1 entries (nf); FP64.  Synchronous. */
 int wz_locality(wz_ctx* ctx, double* f, int nf);
+/* The same probe for another operator: op = WZ_OP_DSLASH (as wz_locality) or
+ * WZ_OP_D, the overlap operator, whose |D(x, 0)| decays exponentially with
+ * the taxi-driver distance (Sec. 3.2, after Hernandez et al.).  Errors as
+ * wz_locality; WZ_EINVAL for another op. */
+int wz_locality_op(wz_ctx* ctx, int op, double* f, int nf);
 
 /* ---- one-loop lattice sums (Sec. 5, Tables sse, fse, ase) ----
  *
@@ -418,6 +429,15 @@ int wz_probe_end(wz_probe_result* out);
  * follows.  No copy is issued and nothing is left in flight.  Runs on the
  * current device, synchronous. */
 int wz_selftest_wait_timeout(int polls, int* status, long long* cycles);
+
+/* FMA throughput of the current device (measurement, not part of the method):
+ * 8 SM-resident blocks of 256 threads per SM, each thread running 8
+ * independent chains of `iters` fused multiply-adds in FP64 (real_bytes 8) or
+ * FP32 (4); *tflops = 2 x FMAs / event time of one launch after a warm-up,
+ * *ms that time.  The roofline of the arithmetic-bound FP64 passes uses the
+ * FP64 figure.  1 <= iters <= 2^24.  Synchronous; allocates and frees a small
+ * output buffer. */
+int wz_fma_peak(int real_bytes, int iters, double* tflops, double* ms);
 
 #ifdef __cplusplus
 }

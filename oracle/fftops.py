@@ -49,6 +49,15 @@ def apply_dslash(psi, r=1.0, M0=1.0, sign=+1.0):
     return ifft4_fermion(sign * spin_mult(Dp, fft4_fermion(psi)))
 
 
+def apply_overlap(psi, r=1.0, M0=1.0):
+    """D psi with the overlap operator D = 1 - V, V = A (A^dag A)^-1/2, applied as
+    FFT -> multiply by D(p) = 1 - (b(p) - i gamma.sin p)/omega(p) -> inverse FFT
+    (Sec. 2.2; the kernel of Sec. 3.1's Eq. d1mom in momentum space)."""
+    dims = psi.shape[:4]
+    Dp = momentum.overlap_D(dims, r, M0)
+    return ifft4_fermion(spin_mult(Dp, fft4_fermion(psi)))
+
+
 def site_terms(params, phi):
     """(y_plus, y_minus): coefficients of P_+ and P_- in Y(x) (Eq. fmat)."""
     c = params.yukawa

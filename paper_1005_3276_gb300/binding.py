@@ -18,10 +18,10 @@ LIBPATH = os.path.join(HERE, "libwz.so")
 WZ_OK, WZ_EINVAL, WZ_ENOMEM, WZ_ECUDA, WZ_NOT_CONVERGED, WZ_EUNSUPPORTED, WZ_ETIMEOUT, WZ_ENONFINITE = range(8)
 WZ_C64, WZ_C128 = 0, 1
 (WZ_OP_M, WZ_OP_MDAG, WZ_OP_MDAGM, WZ_OP_DSLASH, WZ_OP_M0INV, WZ_OP_M0INV_DAG,
- WZ_OP_MTILDE, WZ_OP_MTILDE_DAG, WZ_OP_MTILDE_DAGM, WZ_OP_D1) = range(10)
+ WZ_OP_MTILDE, WZ_OP_MTILDE_DAG, WZ_OP_MTILDE_DAGM, WZ_OP_D1, WZ_OP_D) = range(11)
 OPS = {"M": WZ_OP_M, "Mdag": WZ_OP_MDAG, "MdagM": WZ_OP_MDAGM, "Dslash": WZ_OP_DSLASH,
        "M0inv": WZ_OP_M0INV, "M0inv_dag": WZ_OP_M0INV_DAG, "Mtilde": WZ_OP_MTILDE,
-       "Mtilde_dag": WZ_OP_MTILDE_DAG, "Mtilde_dagM": WZ_OP_MTILDE_DAGM, "D1": WZ_OP_D1}
+       "Mtilde_dag": WZ_OP_MTILDE_DAG, "Mtilde_dagM": WZ_OP_MTILDE_DAGM, "D1": WZ_OP_D1, "D": WZ_OP_D}
 
 
 class WzParams(ctypes.Structure):
@@ -33,7 +33,8 @@ class WzParams(ctypes.Structure):
 class WzSolveStats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("total_iterations", ctypes.c_int),
                 ("reliable_updates", ctypes.c_int), ("converged", ctypes.c_int),
-                ("max_true_residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+                ("max_true_residual", ctypes.c_double), ("seconds", ctypes.c_double),
+                ("site_applies", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -155,10 +156,12 @@ def _load():
         "wz_one_loop": ([I, D, ctypes.POINTER(D)], I),
         "wz_aux_vev": ([P, ctypes.POINTER(D)], I),
         "wz_locality": ([P, ctypes.POINTER(D), I], I),
+        "wz_locality_op": ([P, I, ctypes.POINTER(D), I], I),
         "wz_kernel_launches": ([], ctypes.c_ulonglong),
         "wz_set_workspace_limit": ([P, ctypes.c_size_t], I),
         "wz_workspace_bytes": ([P], ctypes.c_size_t),
         "wz_selftest_wait_timeout": ([I, ctypes.POINTER(I), ctypes.POINTER(ctypes.c_longlong)], I),
+        "wz_fma_peak": ([I, I, ctypes.POINTER(D), ctypes.POINTER(D)], I),
         "wz_probe_begin": ([I, I], I),
         "wz_probe_end": ([ctypes.POINTER(WzProbeResult)], I),
     }
@@ -178,7 +181,7 @@ EXPORTS = ("wz_create", "wz_destroy", "wz_last_error", "wz_supported_extent", "w
            "wz_solve_multishift", "wz_rational_minimax", "wz_spectral_bounds", "wz_rational_apply",
            "wz_rhmc_force", "wz_rhmc_trajectory", "wz_ward_identity", "wz_supercurrent", "wz_one_loop",
            "wz_aux_vev", "wz_locality", "wz_kernel_launches", "wz_probe_begin", "wz_probe_end",
-           "wz_selftest_wait_timeout", "wz_set_workspace_limit", "wz_workspace_bytes")
+           "wz_selftest_wait_timeout", "wz_set_workspace_limit", "wz_workspace_bytes", "wz_locality_op", "wz_fma_peak")
 
 
 def _is_torch(x):
@@ -424,12 +427,19 @@ def wz_aux_vev(ctx, nm=1):
     return [complex(out[2 * j], out[2 * j + 1]) for j in range(nm)]
 
 
-def wz_locality(ctx, dims):
-    """f(r), r = 0 .. T/2 + Z/2 + Y/2 + X/2, of Dslash on a point source."""
+def wz_locality(ctx, dims, op=WZ_OP_DSLASH):
+    """f(r), r = 0 .. T/2 + Z/2 + Y/2 + X/2, of Dslash (or the overlap D) on a point source."""
     n = sum(int(d) // 2 for d in dims) + 1
     out = (ctypes.c_double * n)()
-    check(ctx, LIB.wz_locality(ctx, out, n))
+    check(ctx, LIB.wz_locality_op(ctx, OPS.get(op, op), out, n))
     return np.array(list(out))
+
+
+def wz_fma_peak(real_bytes, iters):
+    """(TFLOP/s, ms) of the FMA throughput microkernel in FP64 (8) or FP32 (4)."""
+    tf, ms = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    check(None, LIB.wz_fma_peak(int(real_bytes), int(iters), ctypes.byref(tf), ctypes.byref(ms)))
+    return tf.value, ms.value
 
 
 def wz_selftest_wait_timeout(polls):
@@ -530,8 +540,8 @@ class Lattice:
     def aux_vev(self):
         return wz_aux_vev(self.ctx)[0]
 
-    def locality(self):
-        return wz_locality(self.ctx, self.dims)
+    def locality(self, op="Dslash"):
+        return wz_locality(self.ctx, self.dims, op)
 
     def force(self, eta, grad, tol=1e-10, parts=WZ_FORCE_FERMION | WZ_FORCE_BOSON):
         npf = 0 if eta is None else self._nrhs(eta)

@@ -63,8 +63,8 @@ bool zt_supported(int nz, int nt) {
 struct TableArgs {
   int T, Z, Y, X;
   double r, M0, m2, invV;
-  double *hV, *hdV, *dV, *d2sV, *ksV, *w1V, *w1sV;
-  float *hVf, *hdVf, *dVf, *d2sVf, *ksVf, *w1Vf, *w1sVf;
+  double *hV, *hdV, *dV, *d2sV, *ksV, *w1V, *w1sV, *d2fV;
+  float *hVf, *hdVf, *dVf, *d2sVf, *ksVf, *w1Vf, *w1sVf, *d2fVf;
 };
 
 __global__ void momentum_tables_kernel(TableArgs a) {
@@ -93,6 +93,10 @@ __global__ void momentum_tables_kernel(TableArgs a) {
     a.hdV[j] = h / den * a.invV;
     a.dV[j] = a.invV / den;
     a.w1V[j] = a.invV / omega;
+    // D2 = 1 - b/omega = sum sin^2 / (omega (omega + b)) = h sum sin^2 / (2 omega):
+    // the same value without the cancellation of 1 - b/omega at small p
+    a.d2fV[j] = 0.5 * h * s2 / omega * a.invV;
+    a.d2fVf[j] = (float)a.d2fV[j];
     a.hVf[j] = (float)a.hV[j];
     a.hdVf[j] = (float)a.hdV[j];
     a.dVf[j] = (float)a.dV[j];
@@ -153,7 +157,8 @@ template <typename R> static void carve(Tables<R>& t, R* base, long V, int T, in
   t.ksV = base + 4 * V;
   t.w1V = base + 5 * V;
   t.w1sV = base + 6 * V;
-  R* ax = base + 7 * V;
+  t.d2fV = base + 7 * V;
+  R* ax = base + 8 * V;
   t.sinT = ax;
   t.sinZ = ax + T;
   t.sinY = ax + T + Z;
@@ -167,7 +172,7 @@ template <typename R> static void carve(Tables<R>& t, R* base, long V, int T, in
 static int build_tables(wz_ctx* c) {
   const long V = c->V;
   const long naxis = 5L * c->T + c->Z + c->Y + c->X;
-  const long n = 7 * V + naxis;
+  const long n = 8 * V + naxis;
   WZ_CUDA_TRY(c, cudaMalloc(&c->t64.block, n * sizeof(double)));
   WZ_CUDA_TRY(c, cudaMalloc(&c->t32.block, n * sizeof(float)));
   carve(c->t64, (double*)c->t64.block, V, c->T, c->Z, c->Y, c->X);
@@ -188,6 +193,8 @@ static int build_tables(wz_ctx* c) {
   a.ksV = c->t64.ksV;
   a.w1V = c->t64.w1V;
   a.w1sV = c->t64.w1sV;
+  a.d2fV = c->t64.d2fV;
+  a.d2fVf = c->t32.d2fV;
   a.w1Vf = c->t32.w1V;
   a.w1sVf = c->t32.w1sV;
   a.hVf = c->t32.hV;
@@ -301,6 +308,7 @@ static int solve_common(wz_ctx* c, const void* b, int nb, void* x, const ShiftSp
     stats->reliable_updates = o.reliable_updates;
     stats->converged = o.converged;
     stats->max_true_residual = o.max_true_residual;
+    stats->site_applies = (double)(o.total_iterations + o.reliable_updates) * (double)c->V;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (rc == WZ_NOT_CONVERGED) set_error(c, rc, name + ": maxiter reached before tol");
@@ -465,10 +473,10 @@ int wz_set_phi(wz_ctx* c, const void* phi) { return set_member_phi(c, 0, phi); }
 int wz_apply(wz_ctx* c, int op, int dtype, const void* in, void* out, int nrhs, double shift) {
   if (!c) return WZ_EINVAL;
   if (!in || !out || nrhs < 0) return set_error(c, WZ_EINVAL, "wz_apply: bad argument");
-  if (op < WZ_OP_M || op > WZ_OP_D1) return set_error(c, WZ_EINVAL, "wz_apply: unknown op");
+  if (op < WZ_OP_M || op > WZ_OP_D) return set_error(c, WZ_EINVAL, "wz_apply: unknown op");
   if (nrhs == 0) return WZ_OK;
   if (c->nm > 1 && nrhs % c->nm) return set_error(c, WZ_EINVAL, "wz_apply: nrhs must be a multiple of the members");
-  if (!c->same_mass && op >= WZ_OP_M0INV && op != WZ_OP_DSLASH && op != WZ_OP_D1)
+  if (!c->same_mass && op >= WZ_OP_M0INV && op != WZ_OP_DSLASH && op != WZ_OP_D1 && op != WZ_OP_D)
     return set_error(c, WZ_EINVAL, "wz_apply: M0^-1 operators need one mass for all members");
   if (dtype == WZ_C128) return apply_typed<double>(c, op, in, out, nrhs, shift);
   if (dtype == WZ_C64) return apply_typed<float>(c, op, in, out, nrhs, shift);

@@ -150,6 +150,17 @@ int apply_op(wz_ctx* c, int op, const cplx<R>* in, cplx<R>* out, int nrhs, R shi
       WZ_RUN(inv(XY_INV, nullptr, nullptr, out, nullptr));
       break;
     }
+    case WZ_OP_D: {
+      // the overlap operator D = D1 + D2 = 1 - V (Sec. 2.2): i gamma.sin p / omega + (1 - b/omega)
+      WZ_RUN(fwd(XY_FWD, in));
+      ZTArgs<R> za = zt_args<R>(c, R(1));
+      za.A = A;
+      za.hV = tables<R>(c).w1V;
+      za.dV = tables<R>(c).d2fV;
+      WZ_RUN(launch_zt<R>(c->Z, c->T, ZT_OVERLAP, za, nrhs, st));
+      WZ_RUN(inv(XY_INV, nullptr, nullptr, out, nullptr));
+      break;
+    }
     case WZ_OP_M0INV:
     case WZ_OP_M0INV_DAG:
       WZ_RUN(fwd(XY_FWD, in));

@@ -163,9 +163,11 @@ int wz_batch_solve(wz_batch* b, const void* const* bs, void* const* xs, int nrhs
   for (auto& t : th) t.join();
   SolveOut tot;
   int worst = WZ_OK;
+  double site_applies = 0.0;
   for (int gi = 0; gi < ng; ++gi) {
     if (rcs[gi] != WZ_OK && rcs[gi] != WZ_NOT_CONVERGED) return batch_error(b, rcs[gi], b->groups[gi]->err);
     if (rcs[gi] == WZ_NOT_CONVERGED) worst = WZ_NOT_CONVERGED;
+    site_applies += (double)(outs[gi].total_iterations + outs[gi].reliable_updates) * (double)b->groups[gi]->V;
     tot.iterations = std::max(tot.iterations, outs[gi].iterations);
     tot.total_iterations += outs[gi].total_iterations;
     tot.reliable_updates += outs[gi].reliable_updates;
@@ -178,6 +180,7 @@ int wz_batch_solve(wz_batch* b, const void* const* bs, void* const* xs, int nrhs
     st->reliable_updates = tot.reliable_updates;
     st->converged = tot.converged;
     st->max_true_residual = tot.max_true_residual;
+    st->site_applies = site_applies;
     st->seconds = 0.0;
   }
   return worst;

@@ -598,6 +598,7 @@ int wz_force(wz_ctx* c, const void* eta, int npf, double tol, unsigned parts, vo
     stats->reliable_updates = so.reliable_updates;
     stats->converged = so.converged;
     stats->max_true_residual = so.max_true_residual;
+    stats->site_applies = (double)(so.total_iterations + so.reliable_updates) * (double)c->V;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return rc;
@@ -661,6 +662,7 @@ int wz_action(wz_ctx* c, const void* eta, int npf, double tol, double* S_B, doub
     stats->reliable_updates = so.reliable_updates;
     stats->converged = so.converged;
     stats->max_true_residual = so.max_true_residual;
+    stats->site_applies = (double)(so.total_iterations + so.reliable_updates) * (double)c->V;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return rc;
@@ -696,6 +698,7 @@ int wz_rhmc_force(wz_ctx* c, const void* eta, int npf, const wz_rational* action
     stats->reliable_updates = so.reliable_updates;
     stats->converged = so.converged;
     stats->max_true_residual = so.max_true_residual;
+    stats->site_applies = (double)(so.total_iterations + so.reliable_updates) * (double)c->V;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   return rc;

@@ -20,6 +20,30 @@ static cudaError_t set_smem(Kern k, size_t bytes) {
   return cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Blocks of a persistent kernel that are resident at once on the current
+// device: SMs x blocks per SM (occupancy at the launch's threads and dynamic
+// shared memory), looked up once per device.
+struct ResidentBlocks {
+  int n[64] = {};
+  template <typename Kern>
+  cudaError_t get(Kern k, int threads, size_t smem, int* out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && n[dev] > 0) {
+      *out = n[dev];
+      return cudaSuccess;
+    }
+    int sms = 0, per = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k, threads, smem)) != cudaSuccess) return e;
+    const int r = (per > 0 ? per : 1) * sms;
+    if (dev >= 0 && dev < 64) n[dev] = r;
+    *out = r;
+    return cudaSuccess;
+  }
+};
+
 // The dynamic shared-memory attribute is a property of a kernel on one device:
 // a process that drives several devices sets it once on each of them.
 #define WZ_MAX_DEVICES 64

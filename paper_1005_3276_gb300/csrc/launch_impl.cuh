@@ -130,10 +130,20 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
     cudaError_t e = set_smem_once(zt_pass<R, NZ, NT, MUL>, smem, attr);
     if (e != cudaSuccess) return e;
   }
-  const long grid = (long)nrhs * a.ntiles;
-  if (grid == 0) return cudaSuccess;
+  const long ntot = (long)nrhs * a.ntiles;
+  if (ntot == 0) return cudaSuccess;
+  // persistent grid: at most the blocks resident on the device, balanced so
+  // that every block takes the same number of tiles (ceil(ntot / grid))
+  static ResidentBlocks resident;
+  int gmax = 0;
+  {
+    cudaError_t e = resident.get(zt_pass<R, NZ, NT, MUL>, S::THREADS, smem, &gmax);
+    if (e != cudaSuccess) return e;
+  }
+  const long per = (ntot + gmax - 1) / gmax;
+  const long grid = (ntot + per - 1) / per;
   // the map covers right-hand sides 0 .. rhs0 + nrhs - 1 of A; the last one is reused
-  const R* t0 = (MUL == ZT_DSLASH || MUL == ZT_GRAD) ? a.hV : (MUL == ZT_SCALAR ? a.d2sV : a.hdV);
+  const R* t0 = (MUL == ZT_DSLASH || MUL == ZT_GRAD || MUL == ZT_OVERLAP) ? a.hV : (MUL == ZT_SCALAR ? a.d2sV : a.hdV);
   const R* t1 = (MUL == ZT_DSLASH || MUL == ZT_GRAD) ? nullptr : (MUL == ZT_SCALAR ? a.ksV : a.dV);
   struct MapCache {
     const void* A = nullptr;
@@ -160,11 +170,14 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
     mc.n = a.rhs0 + nrhs;
   }
   const CUtensorMap tm = mc.m, tm0 = mc.m0, tm1 = mc.m1;
-  // one block reads and writes C columns x NZ x NT sites of 4 spins and reads
-  // the momentum tables it needs (1 for Dslash, 2 for M0^-1)
-  const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + (MUL == ZT_DSLASH ? 1 : 2) * sizeof(R));  // ZT_SCALAR: 2 tables too
+  // one tile reads and writes C columns x NZ x NT sites of 4 spins and reads
+  // the momentum tables it needs (1 for Dslash and D1 on scalars, 2 for
+  // M0^-1 and the scalar pair)
+  const int ntab = (MUL == ZT_DSLASH || MUL == ZT_GRAD) ? 1 : 2;
+  const double bytes = (double)C * NZ * NT * (2.0 * 4 * sizeof(cplx<R>) + ntab * sizeof(R));
   return probed(PK_ZT, (int)sizeof(R), bytes, st, [&](unsigned long long* cnt) {
     ZTArgs<R> b = a;
+    b.ntot = (int)ntot;
     b.blk_count = cnt;
     b.probe_inc = (unsigned long long)bytes;
     zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b, tm, tm0, tm1);
@@ -178,6 +191,7 @@ cudaError_t launch_zt_p(int mul, const ZTArgs<R>& a, int nrhs, cudaStream_t st) 
     case ZT_DSLASH: return launch_zt_t<R, NZ, NT, ZT_DSLASH>(a, nrhs, st);
     case ZT_M0INV: return launch_zt_t<R, NZ, NT, ZT_M0INV>(a, nrhs, st);
     case ZT_M0INV_DAG: return launch_zt_t<R, NZ, NT, ZT_M0INV_DAG>(a, nrhs, st);
+    case ZT_OVERLAP: return launch_zt_t<R, NZ, NT, ZT_OVERLAP>(a, nrhs, st);
     case ZT_SCALAR:
       if constexpr (sizeof(R) == 8) return launch_zt_t<R, NZ, NT, ZT_SCALAR>(a, nrhs, st);
       break;

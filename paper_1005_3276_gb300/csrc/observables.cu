@@ -105,8 +105,11 @@ int wz_aux_vev(wz_ctx* c, double* F) {
   return WZ_OK;
 }
 
-int wz_locality(wz_ctx* c, double* f, int nf) {
+int wz_locality(wz_ctx* c, double* f, int nf) { return wz_locality_op(c, WZ_OP_DSLASH, f, nf); }
+
+int wz_locality_op(wz_ctx* c, int op, double* f, int nf) {
   if (!c || !f) return set_error(c, WZ_EINVAL, "wz_locality: null pointer");
+  if (op != WZ_OP_DSLASH && op != WZ_OP_D) return set_error(c, WZ_EINVAL, "wz_locality_op: op must be Dslash or D");
   const int rmax = c->T / 2 + c->Z / 2 + c->Y / 2 + c->X / 2;
   if (nf < rmax + 1) return set_error(c, WZ_EINVAL, "wz_locality: f needs T/2 + Z/2 + Y/2 + X/2 + 1 entries");
   const size_t field = sizeof(cplx<double>) * 4 * (size_t)c->V;
@@ -118,8 +121,8 @@ int wz_locality(wz_ctx* c, double* f, int nf) {
   WZ_CUDA_TRY(c, cudaMemsetAsync(src, 0, field, c->stream));
   WZ_CUDA_TRY(c, cudaMemcpyAsync(src, &one, sizeof(one), cudaMemcpyHostToDevice, c->stream));  // spin 0 at the origin
   WZ_CUDA_TRY(c, cudaMemsetAsync(fmax, 0, sizeof(unsigned long long) * (rmax + 1), c->stream));
-  WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, WZ_OP_DSLASH, 1)));
-  int rc = apply_op<double>(c, WZ_OP_DSLASH, src, psi, 1, 0.0, (cplx<double>*)c->ws_apply.ptr);
+  WZ_CUDA_TRY(c, c->ws_apply.reserve(apply_ws_bytes<double>(c, op, 1)));
+  int rc = apply_op<double>(c, op, src, psi, 1, 0.0, (cplx<double>*)c->ws_apply.ptr);
   if (rc) return rc;
   count_launch();
   const long blocks = (c->V + 255) / 256;

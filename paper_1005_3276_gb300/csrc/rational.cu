@@ -109,6 +109,7 @@ extern "C" int wz_rational_apply(wz_ctx* c, const wz_rational* r, const void* in
     stats->reliable_updates = acc.reliable_updates;
     stats->converged = acc.converged;
     stats->max_true_residual = acc.max_true_residual;
+    stats->site_applies = (double)(acc.total_iterations + acc.reliable_updates) * (double)c->V;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (status == WZ_NOT_CONVERGED) set_error(c, status, "wz_rational_apply: a shifted solve reached maxiter");

@@ -258,6 +258,7 @@ extern "C" int wz_ward_identity(wz_ctx* c, double tol, int maxiter, unsigned fla
     stats->reliable_updates = sol.reliable_updates;
     stats->converged = sol.converged;
     stats->max_true_residual = sol.max_true_residual;
+    stats->site_applies = (double)(sol.total_iterations + sol.reliable_updates) * (double)c->V;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (solve_rc == WZ_NOT_CONVERGED) return set_error(c, WZ_NOT_CONVERGED, "wz_ward_identity: solve reached maxiter");
@@ -510,6 +511,7 @@ extern "C" int wz_supercurrent(wz_ctx* c, const void* w, double tol, int maxiter
     stats->reliable_updates = sol.reliable_updates;
     stats->converged = sol.converged;
     stats->max_true_residual = sol.max_true_residual;
+    stats->site_applies = (double)(sol.total_iterations + sol.reliable_updates) * (double)c->V;
     stats->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   }
   if (solve_rc == WZ_NOT_CONVERGED) return set_error(c, WZ_NOT_CONVERGED, "wz_supercurrent: solve reached maxiter");

@@ -23,6 +23,7 @@ template <typename R> struct Tables {
   R* ksV = nullptr;   // scalar K(p)/V = (1 - D2/2)/V
   R* w1V = nullptr;   // 1/(omega(p) V), fermion grid: D1(p) = i gamma.sin p / omega
   R* w1sV = nullptr;  // 1/(omega(p) V), periodic (scalar) grid
+  R* d2fV = nullptr;  // D2(p)/V = (1 - b/omega)/V, fermion grid: overlap D = D1 + D2
   R* sinT = nullptr;
   R* sinZ = nullptr;
   R* sinY = nullptr;

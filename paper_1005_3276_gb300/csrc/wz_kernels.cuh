@@ -323,6 +323,8 @@ enum ZTMul {
   ZT_SCALAR,       // periodic scalar pair packed in spin slots: slot 0 *= D2(p), slot 1 *= K(p)
   ZT_GRAD,         // periodic scalar copied into the four slots: slot mu *= i sin p_mu / omega(p)
                    // (the components of D1 acting on a scalar field; table in hV = 1/(omega V))
+  ZT_OVERLAP,      // out = (D2(p) + i gamma.sin p / omega(p)) in: the overlap D = D1 + D2 (Sec. 2.2);
+                   // tables in hV = 1/(omega V) and dV = D2/V
 };
 
 template <typename R> struct ZTArgs {
@@ -342,25 +344,25 @@ template <typename R> struct ZTArgs {
   R m_re, m_im;
   int ntiles;          // ceil(XY / C)
   int X, XY;
-  const int* gate;     // optional per-RHS run flag: block returns if gate[rhs * gate_stride] == 0
+  const int* gate;     // optional per-RHS run flag: tiles of rhs are skipped if gate[rhs * gate_stride] == 0
   int gate_stride;
   int* fail;           // WZ_ETIMEOUT (copy wait ran out) or WZ_ECUDA (misaligned tile) at fail[rhs * fail_stride]
   int fail_stride;
   int rhs0;            // first right-hand side of this launch (launches may cover a group of RHS)
+  int ntot;            // tiles of this launch: (right-hand sides of the launch) x ntiles (set by the launcher)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
-  unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
+  unsigned long long probe_inc;   // probe: algorithmic bytes one tile moves
 };
 
-// Columns per block: 256 B contiguous per (z, t) row for short lines, fewer
-// columns for long lines so that a block stays at <= 512 threads.
+// Columns per tile: C0 columns (8 C0 B FP32 / 16 C0 B FP64 contiguous per
+// (z, t) row) for lines up to 16; one column for 32-point lines, whose tiles
+// are 32 KB (FP32) already and whose threads need the registers of a
+// 32-point line.
 #ifndef WZ_ZT_C0
 #define WZ_ZT_C0 4
 #endif
 template <typename R, int NMAX> struct ZTTile {
-  // C0 columns = 8 C0 B (FP32) / 16 C0 B (FP64) contiguous per (z, t) row;
-  // 4 at 16^2 gives 256-thread blocks (measured against 2 on the 16^4 solve)
-  static constexpr int C0 = WZ_ZT_C0;
-  static constexpr int C = NMAX <= 16 ? C0 : (NMAX <= 32 ? C0 / 2 : C0 / 4);
+  static constexpr int C = NMAX <= 16 ? WZ_ZT_C0 : 1;
 };
 
 // the tile's columns, doubled until the z-phase threads make whole warps
@@ -372,86 +374,55 @@ template <typename R, int NZ, int NT> struct ZTShape {
   static constexpr int THREADS = NMAX * C * 4;
   // every warp must lie entirely inside or outside the t-phase (it shuffles)
   static_assert((NZ * C * 4) % 32 == 0, "z extent too small for the column tile");
+  // Tiles in flight per block: the FP32 passes are bound by memory and copy
+  // the next tile while they transform the current one (two buffers); the
+  // FP64 passes are bound by arithmetic and keep one buffer.
+  static constexpr int NBUF = sizeof(R) == 4 ? 2 : 1;
+  // register budget, as resident threads per SM the pass is compiled for
+  // (FP32: 768 threads = 85 registers for lines up to 16, 384 = 170 for
+  // 32-point lines; FP64: one block)
+  static constexpr int RESIDENT = sizeof(R) == 8 ? THREADS : (NMAX <= 16 ? 768 : 384);
+  static constexpr int MINB = RESIDENT / THREADS > 0 ? RESIDENT / THREADS : 1;
 };
 
-// One block: C consecutive (p_x, p_y) columns of one right-hand side for all
-// (z, t).  The tile [t][z][c][s] arrives in shared memory with one 3D tensor
-// copy (TMA) and leaves with one tensor store; both FFT phases and the spin
-// multiply work on it in place.  Ragged last tiles: the copy fills columns
-// past X * Y with zeros and the store clips them.  The momentum tables of the
-// multiply ([p_t][p_z][column], one or two of them) come the same way in FP32,
-// as a (CB, NZ, NT) box of CB >= C columns starting at a multiple of CB, CB
-// columns making at least one 16-byte row.  Dynamic shared memory: the tile at the (128-byte
-// aligned) start, the table boxes, the mbarrier; the kernel has no static
-// shared memory, which would move the dynamic start.
+// Dynamic shared memory of zt_pass: NBUF buffers, each a tile [t][z][c][s]
+// at a 128-byte aligned start followed by the staged table boxes, then one
+// mbarrier per buffer.  The momentum tables of the multiply ([p_t][p_z][column],
+// one or two of them) are staged in FP32 for lines up to 16, as a (CB, NZ, NT)
+// box of CB >= C columns starting at a multiple of CB, CB columns making at
+// least one 16-byte row; the FP64 and 32-point passes read them from global
+// memory (L2).  The kernel has no static shared memory, which would move the
+// dynamic start.
 template <typename R, int NZ, int NT, int MUL> struct ZTSmem {
-  static constexpr int C = ZTShape<R, NZ, NT>::C;
+  using S = ZTShape<R, NZ, NT>;
+  static constexpr int C = S::C;
   static constexpr unsigned tile = NZ * NT * C * 4 * sizeof(cplx<R>);
-  // FP32 only: the FP64 passes are arithmetic-bound and keep their blocks per SM
-  static constexpr bool STAGE_TAB = sizeof(R) == 4;
+  static constexpr bool STAGE_TAB = sizeof(R) == 4 && S::NMAX <= 16;
   static constexpr int CB = (int)(C * sizeof(R)) >= 16 ? C : (int)(16 / sizeof(R));  // box columns
   static_assert(CB % C == 0, "a tile's columns must fall inside one table box");
   static constexpr int NTAB = STAGE_TAB ? ((MUL == ZT_DSLASH || MUL == ZT_GRAD) ? 1 : 2) : 0;
   static constexpr unsigned tab = NZ * NT * CB * sizeof(R);
   static constexpr unsigned tab_stride = (tab + 127) & ~127u;  // every box starts 128-byte aligned
-  static constexpr unsigned tab_off = (tile + 127) & ~127u;
-  static constexpr unsigned bar_off = (tab_off + NTAB * tab_stride + 15) & ~15u;
-  static constexpr unsigned total = bar_off + 16;
+  static constexpr unsigned tab_off = (tile + 127) & ~127u;    // within a buffer
+  static constexpr unsigned buf = (tab_off + NTAB * tab_stride + 127) & ~127u;
+  static constexpr unsigned bar_off = S::NBUF * buf;
+  static constexpr unsigned total = bar_off + 8 * S::NBUF;
+  static constexpr unsigned tx_bytes = tile + NTAB * tab;  // bytes one tile's copies deliver
 };
-#ifndef WZ_ZT_RESIDENT_THREADS
-#define WZ_ZT_RESIDENT_THREADS 1024  // FP32 register budget: threads per SM the zt pass is compiled for (1280 measured: no gain)
-#endif
+
+// Forward FFT over (z, t), momentum-space multiply and inverse FFT of one tile
+// in shared memory (all threads of the block; barriers inside).
 template <typename R, int NZ, int NT, int MUL>
-__global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS,
-                                  (sizeof(R) == 4 && ZTShape<R, NZ, NT>::THREADS <= 256)
-                                      ? WZ_ZT_RESIDENT_THREADS / ZTShape<R, NZ, NT>::THREADS
-                                      : 1)
-zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmT0,
-        const __grid_constant__ CUtensorMap tmT1) {
+__device__ __forceinline__ void zt_transform(cplx<R>* sm, const R* tab0, const R* tab1, const ZTArgs<R>& a,
+                                             int tile) {
   using ZS = ZTSmem<R, NZ, NT, MUL>;
   constexpr int C = ZTShape<R, NZ, NT>::C;
-  constexpr int U = sizeof(cplx<R>) / 8;  // 8-byte tensor elements per complex value
-  constexpr unsigned TILE_BYTES = ZS::tile;
-  extern __shared__ unsigned char smem_raw[];
-  cplx<R>* sm = reinterpret_cast<cplx<R>*>(smem_raw);  // [t][z][c][s]
-  const R* tab0 = reinterpret_cast<const R*>(smem_raw + ZS::tab_off);  // [pt][pz][c]
-  const R* tab1 = reinterpret_cast<const R*>(smem_raw + ZS::tab_off + ZS::tab_stride);
-  unsigned long long& bar = *reinterpret_cast<unsigned long long*>(smem_raw + ZS::bar_off);
-
   const int tid = threadIdx.x;
   const int s = tid & 3;
   const int c = (tid >> 2) % C;
   const int q = tid / (4 * C);  // t in the z-phase, z in the t-phase
-  const int rhs = blockIdx.x / a.ntiles + a.rhs0;
-  if (a.gate && !a.gate[(long)rhs * a.gate_stride]) return;  // whole block, before any barrier
-  if (a.blk_count && tid == 0) atomicAdd(a.blk_count, a.probe_inc);
-  const int tile = blockIdx.x % a.ntiles;
   const int col_raw = tile * C + c;  // (p_x, p_y) column = p_x * Y + p_y
   const int col = col_raw < a.XY ? col_raw : 0;  // table lookups of lanes past the ragged end
-
-  // tensor copies need a 128-byte aligned shared-memory tile: checked, the
-  // block records the failure and leaves without any copy if it is not
-  if (__syncthreads_or((smem_u32(sm) & 127u) != 0)) {
-    if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ECUDA;
-    return;
-  }
-  if (tid == 0) {
-    mbar_init(&bar, 1);
-    mbar_fence_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bar, TILE_BYTES + ZS::NTAB * ZS::tab);
-    tma_load_3d(sm, &tmA, tile * C * 4 * U, 0, rhs * NT, &bar);
-    const int tx0 = (tile * C / ZS::CB) * ZS::CB;  // table box start (multiple of CB columns)
-    if constexpr (ZS::NTAB >= 1) tma_load_3d(smem_raw + ZS::tab_off, &tmT0, tx0, 0, 0, &bar);
-    if constexpr (ZS::NTAB >= 2) tma_load_3d(smem_raw + ZS::tab_off + ZS::tab_stride, &tmT1, tx0, 0, 0, &bar);
-  }
-  if (__syncthreads_or(!mbar_wait_bounded(&bar, 0))) {
-    if (tid == 0 && a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ETIMEOUT;
-    mbar_wait_bounded(&bar, 0);
-    return;
-  }
 
   cplx<R> v[NT > NZ ? NT : NZ];
 
@@ -514,6 +485,9 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
       } else if constexpr (MUL == ZT_DSLASH) {
         const R hh = a.sign * (ZS::NTAB ? tab0[tix] : a.hV[pidx]);
         v[pt] = hh * mul_i(g);
+      } else if constexpr (MUL == ZT_OVERLAP) {
+        const R w1 = ZS::NTAB ? tab0[tix] : a.hV[pidx], d2 = ZS::NTAB ? tab1[tix] : a.dV[pidx];
+        v[pt] = w1 * mul_i(g) + d2 * v[pt];
       } else {
         const R hd = ZS::NTAB ? tab0[tix] : a.hdV[pidx], dd = ZS::NTAB ? tab1[tix] : a.dV[pidx];
         // mass on the diagonal: M0^-1 has m^* on P_+ and m on P_-; the dagger swaps
@@ -529,7 +503,7 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
   }
   __syncthreads();
 
-  // ---------------- z-phase (inverse), back into the tile, one tensor store
+  // ---------------- z-phase (inverse), back into the tile
   if (q < NT) {
     const int t = q;
 #pragma unroll
@@ -538,11 +512,112 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
 #pragma unroll
     for (int z = 0; z < NZ; ++z) sm[((t * NZ + z) * C + c) * 4 + s] = v[z];
   }
-  fence_proxy_async_smem();
-  __syncthreads();
+}
+
+// Persistent zt pass.  A tile is C consecutive (p_x, p_y) columns of one
+// right-hand side for all (z, t); the launch covers a.ntot tiles (its
+// right-hand sides times a.ntiles) and block b takes tiles b, b + G, b + 2G,
+// ... (G blocks), skipping the tiles of right-hand sides that are gated off.
+// A tile [t][z][c][s] arrives in shared memory by one 3D tensor copy (TMA)
+// plus its table boxes, is transformed in place, and leaves by one tensor
+// store.  With two buffers the copy of the block's next tile is issued before
+// the current one is transformed, into the buffer whose store has been read
+// out, so loads, transforms and stores of successive tiles overlap.  Ragged
+// last tiles: the copy fills columns past X * Y with zeros, the store clips
+// them.  Every wait is bounded; a wait that runs out marks the right-hand
+// side failed, lets the copies in flight land (bounded) and ends the block.
+template <typename R, int NZ, int NT, int MUL>
+__global__ void __launch_bounds__(ZTShape<R, NZ, NT>::THREADS, ZTShape<R, NZ, NT>::MINB)
+zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmT0,
+        const __grid_constant__ CUtensorMap tmT1) {
+  using S = ZTShape<R, NZ, NT>;
+  using ZS = ZTSmem<R, NZ, NT, MUL>;
+  constexpr int C = S::C;
+  constexpr int NBUF = S::NBUF;
+  constexpr int U = sizeof(cplx<R>) / 8;  // 8-byte tensor elements per complex value
+  extern __shared__ unsigned char smem_raw[];
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + ZS::bar_off);
+  const int tid = threadIdx.x;
+  const int G = gridDim.x;
+
+  // the next tile of this block at or after q whose right-hand side runs
+  // (the gates are not written while the pass runs: every thread agrees)
+  auto next_live = [&](int q) {
+    if (a.gate)
+      while (q < a.ntot && !a.gate[(long)(q / a.ntiles + a.rhs0) * a.gate_stride]) q += G;
+    return q;
+  };
+  int q = next_live(blockIdx.x);
+  if (q >= a.ntot) return;  // whole block, before any barrier
+
+  // tensor copies need 128-byte aligned shared-memory tiles: checked, the
+  // block records the failure and leaves without any copy if they are not
+  if (__syncthreads_or((smem_u32(smem_raw) & 127u) != 0)) {
+    if (tid == 0 && a.fail) a.fail[(long)(q / a.ntiles + a.rhs0) * a.fail_stride] = WZ_ECUDA;
+    return;
+  }
   if (tid == 0) {
-    tma_store_3d(&tmA, tile * C * 4 * U, 0, rhs * NT, sm);
-    bulk_store_commit_and_wait_read();
+#pragma unroll
+    for (int b = 0; b < NBUF; ++b) mbar_init(&bars[b], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  // thread 0: copies of tile qq (tile and table boxes) into buffer b
+  auto issue = [&](int qq, int b) {
+    const int rhs = qq / a.ntiles + a.rhs0, tile = qq % a.ntiles;
+    unsigned char* buf = smem_raw + b * ZS::buf;
+    mbar_arrive_expect_tx(&bars[b], ZS::tx_bytes);
+    tma_load_3d(buf, &tmA, tile * C * 4 * U, 0, rhs * NT, &bars[b]);
+    const int tx0 = (tile * C / ZS::CB) * ZS::CB;  // table box start (multiple of CB columns)
+    if constexpr (ZS::NTAB >= 1) tma_load_3d(buf + ZS::tab_off, &tmT0, tx0, 0, 0, &bars[b]);
+    if constexpr (ZS::NTAB >= 2) tma_load_3d(buf + ZS::tab_off + ZS::tab_stride, &tmT1, tx0, 0, 0, &bars[b]);
+  };
+  if (tid == 0) issue(q, 0);
+
+  unsigned long long ntile = 0;
+  for (int j = 0; q < a.ntot; ++j) {
+    const int b = j % NBUF;
+    const unsigned parity = (unsigned)(j / NBUF) & 1u;  // uses of barrier b so far, mod 2
+    const int qn = next_live(q + G);
+    const int rhs = q / a.ntiles + a.rhs0, tile = q % a.ntiles;
+    if constexpr (NBUF == 2) {
+      // the other buffer held the previous tile: once its store has read it
+      // out, it takes the copy of the next tile
+      if (tid == 0 && qn < a.ntot) {
+        bulk_wait_read_all();
+        issue(qn, b ^ 1);
+      }
+    }
+    if (__syncthreads_or(!mbar_wait_bounded(&bars[b], parity))) {
+      if (tid == 0) {
+        if (a.fail) a.fail[(long)rhs * a.fail_stride] = WZ_ETIMEOUT;
+        if (NBUF == 2 && qn < a.ntot) mbar_wait_bounded(&bars[b ^ 1], (unsigned)((j + 1) / NBUF) & 1u);
+        mbar_wait_bounded(&bars[b], parity);
+        bulk_wait_read_all();
+      }
+      return;
+    }
+    unsigned char* buf = smem_raw + b * ZS::buf;
+    zt_transform<R, NZ, NT, MUL>(reinterpret_cast<cplx<R>*>(buf), reinterpret_cast<const R*>(buf + ZS::tab_off),
+                                 reinterpret_cast<const R*>(buf + ZS::tab_off + ZS::tab_stride), a, tile);
+    fence_proxy_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tma_store_3d(&tmA, tile * C * 4 * U, 0, rhs * NT, buf);
+      bulk_commit();
+      if constexpr (NBUF == 1) {
+        if (qn < a.ntot) {
+          bulk_wait_read_all();
+          issue(qn, 0);
+        }
+      }
+    }
+    ++ntile;
+    q = qn;
+  }
+  if (tid == 0) {
+    bulk_wait_read_all();  // the shared memory must outlive the last store's read
+    if (a.blk_count) atomicAdd(a.blk_count, ntile * a.probe_inc);
   }
 }
 

@@ -91,6 +91,9 @@ def test_batch_64_lattice_workload(wz):
         xs.append(torch.zeros_like(bs[-1]))
     st = bt.solve(bs, xs, ws[0].nrhs, tol=TOL)
     assert st["converged"] == 512 and st["max_true_residual"] <= TOL
+    # site-weighted work: between the smallest and the largest lattice's share
+    n = st["total_iterations"] + st["reliable_updates"]
+    assert 4 ** 4 * n < st["site_applies"] < 16 ** 4 * n
     worst = 0.0
     for i, x in enumerate(ws):
         P = oracle.Params(dims=x.dims, m=x.m, g=x.g)

@@ -74,3 +74,15 @@ def test_workspace_growth_refused_with_enomem(wz):
     xb, bb = x.cpu().numpy(), b.cpu().numpy()
     assert max(ocg.true_residual(P, phi, bb[k], xb[k]) for k in range(4)) <= 1e-10
     lat.close()
+
+
+def test_fma_peak_microkernel(wz):
+    """The FMA throughput microkernel that the FP64 roofline is reported
+    against: finite, positive, and FP32 well above FP64 on this part."""
+    f64, ms64 = wz.wz_fma_peak(8, 2000)
+    f32, ms32 = wz.wz_fma_peak(4, 20000)
+    print(f"FMA throughput: FP64 {f64:.2f} TFLOP/s, FP32 {f32:.1f} TFLOP/s")
+    assert f64 > 0 and f32 > 0 and ms64 > 0 and ms32 > 0
+    assert f32 > 4 * f64
+    with pytest.raises(wz.WzError):
+        wz.wz_fma_peak(2, 10)

@@ -191,6 +191,16 @@ def test_dense_M_matches_fft_apply(which, dense2, dense44):
     assert np.abs(dsl @ g5 + g5 @ dsl).max() < 1e-11
 
 
+@pytest.mark.parametrize("which", ["2", "44"])
+def test_dense_overlap_matches_fft_apply(which, dense2, dense44):
+    """The overlap operator applied through the FFT equals the dense
+    position-space D = 1 - A (A^dag A)^-1/2 of Sec. 2.2 (eigendecomposition of
+    the dense Wilson kernel with the antiperiodic time hop)."""
+    dims, _, _, D = dense2 if which == "2" else dense44
+    for v in rnd_field((3, D.shape[0]), 12):
+        assert rel(fftops.apply_overlap(v.reshape(dims + (4,))).ravel(), D @ v) < 1e-12
+
+
 def test_dense_scalar_D2_matches_fft(dense2):
     dims = (2, 4, 2, 2)
     D2blk = dense.build_scalar_D2(dims)

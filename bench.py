@@ -77,7 +77,9 @@ def parse():
     ap.add_argument("--hmc-therm", type=int, default=4, help="thermalisation trajectories of the HMC start")
     ap.add_argument("--no-sweep", action="store_true", help="skip the L = 8, 16, 32 apply sweep")
     ap.add_argument("--no-solve32", action="store_true", help="skip the 32^4 x 4 RHS mixed solve")
-    ap.add_argument("--no-invtab", action="store_true", help="skip the solver-table shaped L^3 x 32 solves")
+    ap.add_argument("--no-invtab", action="store_true", help="skip the solver-table shaped L^3 x T solves")
+    ap.add_argument("--invtab-full", action="store_true",
+                    help="also the unpreconditioned FP64 solve of the 32^3 x 64 solver-table row")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-lattice batched workload")
     ap.add_argument("--no-rhmc", action="store_true", help="skip the rational heatbath / RHMC timings")
     ap.add_argument("--no-oneloop", action="store_true", help="skip the one-loop lattice sums (Sec. 5 tables)")
@@ -530,19 +532,23 @@ def main():
     invtab = None
     if not args.no_invtab:
         paper = {"8^3x32": {"single": (1.3, 830, 0.038, 8), "double": (4.9, 1600, 0.13, 15)},
-                 "16^3x32": {"single": (7.1, 870, 0.20, 8), "double": (31, 1800, 0.74, 15)}}
-        invtab = {"workload": "L^3 x 32, m = 1, g = 0.2, phi sigma 0.5, 1 complex-Gaussian RHS; "
+                 "16^3x32": {"single": (7.1, 870, 0.20, 8), "double": (31, 1800, 0.74, 15)},
+                 "32^3x64": {"single": (420, 1600, 6.8, 8), "double": (2200, 3900, 25, 15)}}
+        invtab = {"workload": "L^3 x T (8^3 x 32, 16^3 x 32, 32^3 x 64), m = 1, g = 0.2, phi sigma 0.5, "
+                              "1 complex-Gaussian RHS; "
                               "'single' = FP32 iteration with FP64 reliable updates to 1e-6, "
                               "'double' = FP64 to 1e-12 (true residuals)", "rows": []}
-        for L in (8, 16):
-            dims = (32, L, L, L)
+        for L, T in ((8, 32), (16, 32), (32, 64)):
+            dims = (T, L, L, L)
             il = wz.Lattice(dims, m=1.0, g=0.2, stream=stream.cuda_stream)
             il.set_phi(torch.from_numpy(synth.scalar_field(dims, 0.5, 0)).cuda())
             bi = torch.from_numpy(synth.spinor_rhs(1, dims, 1)).cuda()
             xi = torch.zeros_like(bi)
-            row = {"lattice": f"{L}^3x32", "paper_gtx285": paper[f"{L}^3x32"]}
+            row = {"lattice": f"{L}^3x{T}", "paper_gtx285": paper[f"{L}^3x{T}"]}
             for prec, mixed, tol in (("single", True, 1e-6), ("double", False, 1e-12)):
                 for pc in (False, True):
+                    if T == 64 and prec == "double" and not pc and not args.invtab_full:
+                        continue  # thousands of FP64 iterations at 2M sites: --invtab-full
                     il.solve(bi, xi, tol=tol, mixed=mixed, pc=pc)  # warm-up (graph, tuner)
                     torch.cuda.synchronize()
                     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -15,7 +15,9 @@
  * Conventions shared by every call
  * --------------------------------
  * - a = 1.  dims = {T, Z, Y, X}; T even (antiperiodic fermion time, Sec. 3.1);
- *   X == Y; every extent in the supported set returned by wz_supported_extent.
+ *   X == Y in {4, 6, 8, 12, 16, 32} (wz_supported_extent); (Z, T) one of the
+ *   compiled pairs (4, 4), (6, 6), (8, 8), (12, 12), (16, 16), (32, 32),
+ *   (8, 16), (16, 32), (8, 32) and (32, 64), the last the paper's 32^3 x 64.
  * - Spinor field: complex, interleaved (re, im), layout [nrhs][T][Z][Y][X][4],
  *   spin index fastest.  WZ_C64 = complex64 (2 x float), WZ_C128 = complex128.
  * - Scalar field phi: complex128 [T][Z][Y][X], periodic in every direction.

@@ -41,11 +41,7 @@ template <typename R> static XYArgs<R> xy_args(const wz_ctx* c, int nrhs) {
 }
 
 // the column tile of zt_pass<R, nz, nt> (ZTShape::C), from the runtime extents
-template <typename R> static int zt_cols(int nz, int nt) {
-  const int n = nz > nt ? nz : nt;
-  const int c = n <= 16 ? ZTTile<R, 16>::C : (n <= 32 ? ZTTile<R, 32>::C : ZTTile<R, 64>::C);
-  return zt_columns(c, nz);
-}
+template <typename R> static int zt_cols(int nz, int nt) { return zt_cols_of<R>(nz, nt); }
 
 template <typename R> static ZTArgs<R> zt_args(const wz_ctx* c, R sign) {
   const Tables<R>& t = tables<R>(c);

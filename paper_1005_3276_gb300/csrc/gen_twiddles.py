@@ -1,13 +1,16 @@
-"""Write twiddles.h: cos(2 pi k / 192) for k = 0..191 as double literals.
+"""Write twiddles.h: cos(2 pi k / 384) for k = 0..383 as double literals.
 
-192 = 2^6 * 3 covers every FFT length the kernels use (N divides 192).  Values
-are taken from the first octant (k <= 24) with the host libm and extended by
-the exact symmetries of cosine, so cos(pi/2) = 0 and cos(pi/3) = 1/2 exactly.
+384 = 2^7 * 3 covers every FFT length the kernels use (N divides 384) and the
+antiperiodic time momenta pi (2n + 1) / T up to T = 64 (2 T divides 384).
+Values are taken from the first octant (k <= 48) with the host libm and
+extended by the exact symmetries of cosine, so cos(pi/2) = 0 and
+cos(pi/3) = 1/2 exactly.  The angle 2 pi k / 384 is the same double as
+2 pi (k/2) / 192 for even k, so the entries of a shorter table are unchanged.
 Run from this directory: python gen_twiddles.py
 """
 import math
 
-N = 192
+N = 384
 
 
 def first_octant(k):
@@ -33,16 +36,16 @@ def cos_exact(k):
 
 
 vals = [cos_exact(k) for k in range(N)]
-vals[32] = 0.5   # cos(pi/3)
-vals[160] = 0.5
-vals[64] = -0.5  # cos(2 pi/3)
-vals[128] = -0.5
+vals[N // 6] = 0.5       # cos(pi/3)
+vals[5 * N // 6] = 0.5
+vals[N // 3] = -0.5      # cos(2 pi/3)
+vals[2 * N // 3] = -0.5
 rows = []
 for i in range(0, N, 4):
     rows.append("    " + ", ".join(repr(v) for v in vals[i:i + 4]) + ",")
 with open("twiddles.h", "w") as f:
-    f.write("// Generated by gen_twiddles.py: cos(2 pi k / 192), k = 0..191.\n")
+    f.write(f"// Generated by gen_twiddles.py: cos(2 pi k / {N}), k = 0..{N - 1}.\n")
     f.write("#pragma once\n")
-    f.write("#define WZ_TW_N 192\n")
+    f.write(f"#define WZ_TW_N {N}\n")
     f.write("#define WZ_TW_TABLE \\\n")
     f.write(" \\\n".join(rows) + "\n")

@@ -8,7 +8,7 @@
 
 // extents with compiled kernels; the xy pass needs X == Y, the zt pass a (Z, T) pair
 #define WZ_FOR_EXTENTS(F) F(4) F(6) F(8) F(12) F(16) F(32)
-#define WZ_FOR_ZT_PAIRS(F) F(4, 4) F(6, 6) F(8, 8) F(12, 12) F(16, 16) F(32, 32) F(8, 16) F(16, 32) F(8, 32)
+#define WZ_FOR_ZT_PAIRS(F) F(4, 4) F(6, 6) F(8, 8) F(12, 12) F(16, 16) F(32, 32) F(8, 16) F(16, 32) F(8, 32) F(32, 64)
 
 namespace wz {
 

@@ -365,23 +365,37 @@ template <typename R, int NMAX> struct ZTTile {
   static constexpr int C = NMAX <= 16 ? WZ_ZT_C0 : 1;
 };
 
+// Spin components per thread: FP32 lines up to 16 hold the two adjacent
+// spins of one chirality (16-byte shared-memory accesses, two independent
+// FFT chains, half the shuffles of the spin multiply); FP64 and 32-point
+// lines hold one (register budget).
+template <typename R> constexpr int zt_spt(int nmax) { return (sizeof(R) == 4 && nmax <= 16) ? 2 : 1; }
+
 // the tile's columns, doubled until the z-phase threads make whole warps
-constexpr int zt_columns(int c, int nz) { return (nz * c * 4) % 32 ? zt_columns(2 * c, nz) : c; }
+constexpr int zt_columns(int c, int nz, int tpc) { return (nz * c * tpc) % 32 ? zt_columns(2 * c, nz, tpc) : c; }
+
+// the column count of zt_pass<R, nz, nt> (ZTShape::C), also from run-time extents
+template <typename R> constexpr int zt_cols_of(int nz, int nt) {
+  return zt_columns((nz > nt ? nz : nt) <= 16 ? WZ_ZT_C0 : 1, nz, 4 / zt_spt<R>(nz > nt ? nz : nt));
+}
 
 template <typename R, int NZ, int NT> struct ZTShape {
   static constexpr int NMAX = NZ > NT ? NZ : NT;
-  static constexpr int C = zt_columns(ZTTile<R, NMAX>::C, NZ);
-  static constexpr int THREADS = NMAX * C * 4;
+  static constexpr int SPT = zt_spt<R>(NMAX);
+  static constexpr int TPC = 4 / SPT;  // threads per (line, column)
+  static constexpr int C = zt_cols_of<R>(NZ, NT);
+  static constexpr int THREADS = NMAX * C * TPC;
+  static_assert(C == zt_columns(ZTTile<R, NMAX>::C, NZ, TPC), "column rule");
   // every warp must lie entirely inside or outside the t-phase (it shuffles)
-  static_assert((NZ * C * 4) % 32 == 0, "z extent too small for the column tile");
+  static_assert((NZ * C * TPC) % 32 == 0, "z extent too small for the column tile");
   // Tiles in flight per block: the FP32 passes are bound by memory and copy
   // the next tile while they transform the current one (two buffers); the
   // FP64 passes are bound by arithmetic and keep one buffer.
   static constexpr int NBUF = sizeof(R) == 4 ? 2 : 1;
   // register budget, as resident threads per SM the pass is compiled for
-  // (FP32: 768 threads = 85 registers for lines up to 16, 384 = 170 for
-  // 32-point lines; FP64: one block)
-  static constexpr int RESIDENT = sizeof(R) == 8 ? THREADS : (NMAX <= 16 ? 768 : 384);
+  // (FP32: 384 threads = 170 registers, two 16-point lines or one 32-point
+  // line a thread; FP64: one block)
+  static constexpr int RESIDENT = sizeof(R) == 8 ? THREADS : 384;
   static constexpr int MINB = RESIDENT / THREADS > 0 ? RESIDENT / THREADS : 1;
 };
 
@@ -412,9 +426,26 @@ template <typename R, int NZ, int NT, int MUL> struct ZTSmem {
 
 // Forward FFT over (z, t), momentum-space multiply and inverse FFT of one tile
 // in shared memory (all threads of the block; barriers inside).
+// The per-axis sin p of a thread's t-phase column, loaded before the z-phase so
+// that their latency is hidden behind it.
+template <typename R> struct ZTSin {
+  R x, y, z;
+};
+template <typename R, int NZ, int NT>
+__device__ __forceinline__ ZTSin<R> zt_sines(const ZTArgs<R>& a, int tile) {
+  using S = ZTShape<R, NZ, NT>;
+  const int c = (threadIdx.x / S::TPC) % S::C;
+  const int pz = threadIdx.x / (S::TPC * S::C);
+  const int col_raw = tile * S::C + c;
+  const int col = col_raw < a.XY ? col_raw : 0;
+  const int px = col / a.X, py = col - px * a.X;  // momentum planes are xy-transposed (X == Y)
+  return ZTSin<R>{__ldg(a.sinX + px), __ldg(a.sinY + py), __ldg(a.sinZ + (pz < NZ ? pz : 0))};
+}
+
+// one spin component per thread
 template <typename R, int NZ, int NT, int MUL>
-__device__ __forceinline__ void zt_transform(cplx<R>* sm, const R* tab0, const R* tab1, const ZTArgs<R>& a,
-                                             int tile) {
+__device__ __forceinline__ void zt_transform1(cplx<R>* sm, const R* tab0, const R* tab1, const ZTArgs<R>& a,
+                                              int tile, ZTSin<R> sn) {
   using ZS = ZTSmem<R, NZ, NT, MUL>;
   constexpr int C = ZTShape<R, NZ, NT>::C;
   const int tid = threadIdx.x;
@@ -445,9 +476,7 @@ __device__ __forceinline__ void zt_transform(cplx<R>* sm, const R* tab0, const R
     for (int t = 0; t < NT; ++t) v[t] = sm[((t * NZ + pz) * C + c) * 4 + s];
     fft_ptr<NT, -1, R>(v);
 
-    // momentum planes are xy-transposed: column = p_x * Y + p_y (X == Y)
-    const int px = col / a.X, py = col - px * a.X;
-    const R sx = a.sinX[px], sy = a.sinY[py], sz = a.sinZ[pz];
+    const R sx = sn.x, sy = sn.y, sz = sn.z;
     const int lane = threadIdx.x & 31;
     const int ulane = (lane & ~3) | (s < 2 ? 2 : 0);  // opposite-chirality pair
     const R sg = s < 2 ? R(1) : R(-1);
@@ -514,6 +543,132 @@ __device__ __forceinline__ void zt_transform(cplx<R>* sm, const R* tab0, const R
   }
 }
 
+// Two spin components (2h, 2h + 1: one chirality) per thread, FP32.  The
+// multiply needs the other chirality's pair, which the partner thread (lane
+// ^ 1) holds: two complex shuffles give both of this thread's outputs.
+template <int NZ, int NT, int MUL>
+__device__ __forceinline__ void zt_transform2(cplx<float>* sm, const float* tab0, const float* tab1,
+                                              const ZTArgs<float>& a, int tile, ZTSin<float> sn) {
+  using R = float;
+  using ZS = ZTSmem<R, NZ, NT, MUL>;
+  constexpr int C = ZTShape<R, NZ, NT>::C;
+  const int tid = threadIdx.x;
+  const int h = tid & 1;           // spin pair: components 2h, 2h + 1
+  const int c = (tid >> 1) % C;
+  const int q = tid / (2 * C);     // t in the z-phase, z in the t-phase
+  float4* sm4 = reinterpret_cast<float4*>(sm);  // [t][z][c][h]: one spin pair per 16 bytes
+  constexpr int N = NT > NZ ? NT : NZ;
+  cplx<R> v0[N], v1[N];
+
+  // ---------------- z-phase (forward): thread owns (t = q, column, pair)
+  if (q < NT) {
+    const int t = q;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+      const float4 f = sm4[((t * NZ + z) * C + c) * 2 + h];
+      v0[z] = cplx<R>{f.x, f.y};
+      v1[z] = cplx<R>{f.z, f.w};
+    }
+    fft_ptr<NZ, -1, R>(v0);
+    fft_ptr<NZ, -1, R>(v1);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) sm4[((t * NZ + z) * C + c) * 2 + h] = make_float4(v0[z].x, v0[z].y, v1[z].x, v1[z].y);
+  }
+  __syncthreads();
+
+  // ---------------- t-phase: forward over t, spin multiply, inverse over t
+  if (q < NZ) {
+    const int pz = q;
+#pragma unroll
+    for (int t = 0; t < NT; ++t) {
+      const float4 f = sm4[((t * NZ + pz) * C + c) * 2 + h];
+      v0[t] = cplx<R>{f.x, f.y};
+      v1[t] = cplx<R>{f.z, f.w};
+    }
+    fft_ptr<NT, -1, R>(v0);
+    fft_ptr<NT, -1, R>(v1);
+
+    const R sx = sn.x, sy = sn.y, sz = sn.z;
+    const int partner = (threadIdx.x & 31) ^ 1;
+    const R sg = h == 0 ? R(1) : R(-1);  // +1 on P_- (spins 0, 1), -1 on P_+ (spins 2, 3)
+    const cplx<R> ue{R(0), sg * sz}, we{sg * sy, sg * sx};      // even spin: (st + i sg sz) u + (sg sy + i sg sx) w
+    const cplx<R> uo{-sg * sy, sg * sx}, wo{R(0), -sg * sz};    // odd spin: (-sg sy + i sg sx) u + (st - i sg sz) w
+#pragma unroll
+    for (int pt = 0; pt < NT; ++pt) {
+      const int tix = (pt * NZ + pz) * ZS::CB + (tile * C) % ZS::CB + c;  // staged tables
+      static_assert(WZ_TW_N % (2 * NT) == 0, "antiperiodic momenta must lie on the twiddle grid");
+      const R st = Tw<R>::cosk(((2 * pt + 1) * (WZ_TW_N / (2 * NT)) + 3 * WZ_TW_N / 4) % WZ_TW_N);
+      if constexpr (MUL == ZT_SCALAR) {
+        // slot 0 *= D2(p), slot 1 *= K(p), slots 2, 3 = 0 (periodic scalar pair)
+        v0[pt] = (h == 0 ? tab0[tix] : R(0)) * v0[pt];
+        v1[pt] = (h == 0 ? tab1[tix] : R(0)) * v1[pt];
+      } else if constexpr (MUL == ZT_GRAD) {
+        static_assert(WZ_TW_N % NT == 0, "periodic momenta must lie on the twiddle grid");
+        const R stp = Tw<R>::cosk((pt * (WZ_TW_N / NT) + 3 * WZ_TW_N / 4) % WZ_TW_N);
+        const R w1 = tab0[tix];
+        v0[pt] = ((h == 0 ? stp : sy) * w1) * mul_i(v0[pt]);  // slots 0 (t) / 2 (y)
+        v1[pt] = ((h == 0 ? sx : sz) * w1) * mul_i(v1[pt]);   // slots 1 (x) / 3 (z)
+      } else {
+        cplx<R> u, w;  // the other chirality's pair (even, odd) at this momentum
+        u.x = __shfl_sync(0xffffffffu, v0[pt].x, partner);
+        u.y = __shfl_sync(0xffffffffu, v0[pt].y, partner);
+        w.x = __shfl_sync(0xffffffffu, v1[pt].x, partner);
+        w.y = __shfl_sync(0xffffffffu, v1[pt].y, partner);
+        const cplx<R> ge = cplx<R>{st, ue.y} * u + we * w;  // (gamma . sin p  in) of the even spin
+        const cplx<R> go = uo * u + cplx<R>{st, wo.y} * w;  // ... of the odd spin
+        if constexpr (MUL == ZT_DSLASH) {
+          const R hh = a.sign * tab0[tix];
+          v0[pt] = hh * mul_i(ge);
+          v1[pt] = hh * mul_i(go);
+        } else if constexpr (MUL == ZT_OVERLAP) {
+          const R w1 = tab0[tix], d2 = tab1[tix];
+          v0[pt] = w1 * mul_i(ge) + d2 * v0[pt];
+          v1[pt] = w1 * mul_i(go) + d2 * v1[pt];
+        } else {
+          const R hd = tab0[tix], dd = tab1[tix];
+          // mass on the diagonal: M0^-1 has m^* on P_+ and m on P_-; the dagger swaps
+          const bool mconj = (MUL == ZT_M0INV) ? (h == 1) : (h == 0);
+          const cplx<R> mm{a.m_re, mconj ? -a.m_im : a.m_im};
+          const R sd = (MUL == ZT_M0INV) ? R(-1) : R(1);
+          v0[pt] = (sd * hd) * mul_i(ge) + dd * (mm * v0[pt]);
+          v1[pt] = (sd * hd) * mul_i(go) + dd * (mm * v1[pt]);
+        }
+      }
+    }
+    fft_ptr<NT, +1, R>(v0);
+    fft_ptr<NT, +1, R>(v1);
+#pragma unroll
+    for (int t = 0; t < NT; ++t) sm4[((t * NZ + pz) * C + c) * 2 + h] = make_float4(v0[t].x, v0[t].y, v1[t].x, v1[t].y);
+  }
+  __syncthreads();
+
+  // ---------------- z-phase (inverse), back into the tile
+  if (q < NT) {
+    const int t = q;
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) {
+      const float4 f = sm4[((t * NZ + z) * C + c) * 2 + h];
+      v0[z] = cplx<R>{f.x, f.y};
+      v1[z] = cplx<R>{f.z, f.w};
+    }
+    fft_ptr<NZ, +1, R>(v0);
+    fft_ptr<NZ, +1, R>(v1);
+#pragma unroll
+    for (int z = 0; z < NZ; ++z) sm4[((t * NZ + z) * C + c) * 2 + h] = make_float4(v0[z].x, v0[z].y, v1[z].x, v1[z].y);
+  }
+}
+
+template <typename R, int NZ, int NT, int MUL>
+__device__ __forceinline__ void zt_transform(cplx<R>* sm, const R* tab0, const R* tab1, const ZTArgs<R>& a,
+                                             int tile, ZTSin<R> sn) {
+  if constexpr (ZTShape<R, NZ, NT>::SPT == 2) {
+    static_assert(sizeof(R) == 4 && ZTSmem<R, NZ, NT, MUL>::NTAB > 0, "two spins a thread: FP32, staged tables");
+    zt_transform2<NZ, NT, MUL>(sm, tab0, tab1, a, tile, sn);
+  } else {
+    zt_transform1<R, NZ, NT, MUL>(sm, tab0, tab1, a, tile, sn);
+  }
+}
+
 // Persistent zt pass.  A tile is C consecutive (p_x, p_y) columns of one
 // right-hand side for all (z, t); the launch covers a.ntot tiles (its
 // right-hand sides times a.ntiles) and block b takes tiles b, b + G, b + 2G,
@@ -575,11 +730,12 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
   if (tid == 0) issue(q, 0);
 
   unsigned long long ntile = 0;
+  int qn = next_live(q + G);
   for (int j = 0; q < a.ntot; ++j) {
     const int b = j % NBUF;
     const unsigned parity = (unsigned)(j / NBUF) & 1u;  // uses of barrier b so far, mod 2
-    const int qn = next_live(q + G);
     const int rhs = q / a.ntiles + a.rhs0, tile = q % a.ntiles;
+    const ZTSin<R> sn = zt_sines<R, NZ, NT>(a, tile);
     if constexpr (NBUF == 2) {
       // the other buffer held the previous tile: once its store has read it
       // out, it takes the copy of the next tile
@@ -598,8 +754,10 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
       return;
     }
     unsigned char* buf = smem_raw + b * ZS::buf;
+    // the tile after next: its gate is read while this tile is transformed
+    const int qnn = qn < a.ntot ? next_live(qn + G) : qn;
     zt_transform<R, NZ, NT, MUL>(reinterpret_cast<cplx<R>*>(buf), reinterpret_cast<const R*>(buf + ZS::tab_off),
-                                 reinterpret_cast<const R*>(buf + ZS::tab_off + ZS::tab_stride), a, tile);
+                                 reinterpret_cast<const R*>(buf + ZS::tab_off + ZS::tab_stride), a, tile, sn);
     fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
@@ -614,6 +772,7 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
     }
     ++ntile;
     q = qn;
+    qn = qnn;
   }
   if (tid == 0) {
     bulk_wait_read_all();  // the shared memory must outlive the last store's read

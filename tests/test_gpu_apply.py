@@ -109,10 +109,11 @@ def test_empty_batch_is_noop(wz):
     lat.apply("M", x, x, 0)
 
 
-@pytest.mark.parametrize("dims", [(32, 32, 32, 32), (32, 16, 16, 16)])
+@pytest.mark.parametrize("dims", [(32, 32, 32, 32), (32, 16, 16, 16), (64, 32, 32, 32)])
 @pytest.mark.parametrize("dt", ["c128", "c64"])
 def test_apply_L32(wz, dims, dt):
-    """32-point lines (the 32^4 workload and the L = 32 apply sweep)."""
+    """32-point lines (the 32^4 workload and the L = 32 apply sweep) and the
+    paper's largest lattice 32^3 x 64 (64-point time lines)."""
     P = oracle.Params(dims=dims, m=0.02, g=1.0)
     phi = synth.scalar_field(dims, 1.0, 0)
     psi = synth.spinor_rhs(1, dims, 1)

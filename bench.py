@@ -11,11 +11,29 @@ applies = sum over right-hand sides of the CG iterations (one FP32 M^dagger M
 each) plus the FP64 M^dagger M applies of the reliable updates.  The inputs
 are resident on the device; L2 is flushed (256 MB write) before every step.
 
-Extra keys: the same solve in FP64 throughout (the baseline the mixed path
-must beat), "e2e" through the C ABI with host buffers, a roofline of the
-dominant kernel from the library's event probe, the FP64 CPU oracle timed on
-a bounded sample, SM clocks sampled during the timed region, and the count of
-library kernels launched in the timed region.
+Extra keys (all on the same GPU, after the timed steps):
+  fp64            the same solve in FP64 throughout, also against the measured
+                  FP64 FMA throughput (fma_peak_TFLOP_s, the project's microkernel)
+  kernels         every kernel class of one solve, probed one launch at a time
+                  (CUDA events per launch, algorithmic bytes of the same launches);
+                  roofline = the class with the most time per solve
+  solve_roofline  the whole CG iteration against HBM (592 B per site-RHS)
+  solve_32x4      the mixed solve at 32^4 x 4 RHS, a working set far beyond L2
+  apply_sweep     M^dag M applies at L = 8, 16, 32, FP32 and FP64, L2 flushed
+                  before every repetition, with the zt and xy passes probed
+  hmc             trajectories/s of the 16^4 differentiation workload: one
+                  lattice and a batch of independent replicas, mixed and FP64,
+                  from thermalised configurations (acceptance, dH, HBM fraction)
+  batch           the 64-lattice batching workload (16 each of 4^4..16^4)
+  large           the 32^4 workload: an Omelyan trajectory with 4 pseudofermions
+                  (2 of its 40 steps by default) and the measurements of the new
+                  configuration (<F~>, Ward identity, supercurrent correlators)
+  rhmc, one_loop, paper_solver_table
+                  rational heatbath, RHMC trajectory, one-loop sums and the
+                  solver-table runs, each beside the paper's printed numbers
+  e2e             the headline through the C ABI with host buffers
+  cpu_baseline    the FP64 CPU oracle on a bounded sample
+  clocks          SM clocks and throttle reasons sampled during the timed steps
 
 --impl reference times the FP64 CPU oracle (the plain definitions) on the
 host cores with the same metric.  Under torchrun every rank runs its own
@@ -71,6 +89,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end solve")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--oracle-sample", type=float, default=0.0, help=argparse.SUPPRESS)
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory timing")
     ap.add_argument("--hmc-traj", type=int, default=2, help="timed mixed trajectories (FP64: half, batched: 1)")
     ap.add_argument("--hmc-replicas", type=int, default=8, help="independent 16^4 replicas of the batched HMC")
@@ -139,7 +158,8 @@ TRAFFIC_SOURCES = ("wz_kernels.cuh", "wz_cg.cuh", "wz_fft.cuh", "wz_tma.cuh", "l
 
 # kernel classes of one mixed solve: FP32 iteration passes and the FP64
 # reliable-update passes (zt runs in both precisions)
-PROBE_CLASSES = (("zt", 4), ("cg_p1", 4), ("cg_p3", 4), ("cg_p5", 4), ("zt", 8), ("ru_p1", 8), ("ru_p5", 8))
+PROBE_CLASSES = (("zt", 4), ("cg_p1", 4), ("cg_p3", 4), ("cg_p5", 4), ("zt", 8), ("ru_p1", 8), ("cg_p3", 8),
+                 ("ru_p5", 8))
 
 
 def kernel_table(probes):
@@ -190,6 +210,17 @@ def recorded_traffic(cls, probe, alg_bytes_per_launch):
         return None
     per_rhs, alg_per_rhs = (float(v) for v in rec[kind].split())
     return per_rhs * alg_bytes_per_launch / alg_per_rhs
+
+
+def oracle_sample_one_thread(seconds):
+    """The same oracle sample in a child process whose BLAS / OpenMP pools are
+    limited to one thread: (applies/s, applies, seconds, threads used)."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--oracle-sample", str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=600)
+    if p.returncode != 0:
+        return None
+    return json.loads(p.stdout.strip().splitlines()[-1])
 
 
 def cpu_threads():
@@ -288,6 +319,10 @@ class ClockSampler:
 def main():
     args = parse()
     w = synth.PRECISION_16
+    if args.oracle_sample > 0:
+        v, n, dt = oracle_applies_per_s(w, args.oracle_sample)
+        print(json.dumps({"value": v, "applies": n, "seconds": dt, "cores": cpu_threads()}))
+        return
     if args.impl == "reference":
         run_reference(args, w)
         return
@@ -362,6 +397,22 @@ def main():
         wz.wz_probe_begin(kind, rb)
         solve()
         probes[f"{kind}_fp{8 * rb}"] = wz.wz_probe_end()
+    # the same kernels with one launch per pass covering all right-hand sides
+    # (the group size forced to nrhs): per-kernel efficiency at full launch size
+    probes_full = {}
+    saved = {k: os.environ.get(k) for k in ("WZ_RHS_GROUP", "WZ_RHS_BRANCHES")}
+    os.environ["WZ_RHS_GROUP"], os.environ["WZ_RHS_BRANCHES"] = str(w.nrhs), "1"
+    for kind, rb in PROBE_CLASSES[:4]:
+        flush.zero_()
+        torch.cuda.synchronize()
+        wz.wz_probe_begin(kind, rb)
+        solve()
+        probes_full[f"{kind}_fp{8 * rb}"] = wz.wz_probe_end()
+    for k, v in saved.items():
+        if v is None:
+            os.environ.pop(k, None)
+        else:
+            os.environ[k] = v
 
     t_max, applies_all = combine_ranks(dist, total_ms, total_applies, "cuda")
     value = applies_all / (t_max / 1000.0)
@@ -780,6 +831,13 @@ def main():
                 "algorithmic_bytes_per_launch": k["algorithmic_bytes_per_launch"],
                 "note": "eager single-stream launches of one solve, CUDA events per launch; achieved = "
                         "algorithmic bytes / event time over the same (timed) launches"}
+    kernels_full = kernel_table(probes_full)
+    kf = kernels_full[dom] if dom in kernels_full else None
+    roofline_full = None if kf is None else {
+        "bound": "hbm", "kernel": dom, "achieved": kf["achieved_GB_s"], "peak": peak, "unit": "GB/s",
+        "frac": kf["achieved_GB_s"] / peak if kf["achieved_GB_s"] else None,
+        "avg_launch_us": kf["avg_launch_us"], "algorithmic_bytes_per_launch": kf["algorithmic_bytes_per_launch"],
+        "note": f"the dominant class with one launch per pass covering all {w.nrhs} right-hand sides"}
 
     # the whole CG iteration against the same peak: per M^dag M apply of one RHS
     # the five passes move 18 FP32 spinor fields (P1 6, zt 2 + 2, P3 4, P5 4)
@@ -794,6 +852,11 @@ def main():
         v, n, dt = oracle_applies_per_s(w, args.cpu_seconds)
         cpu = {"value": v, "unit": UNIT, "cores": cpu_threads(), "kind": "oracle",
                "sample": f"FP64 oracle CG iterations on RHS 0 of {w.name}: {n} M^dag M applies in {dt:.1f} s"}
+        one = oracle_sample_one_thread(args.cpu_seconds / 2)
+        if one is not None:
+            cpu["one_thread"] = {"value": one["value"], "cores": one["cores"],
+                                 "sample": f"the same, BLAS/OpenMP limited to one thread: {one['applies']} "
+                                           f"applies in {one['seconds']:.1f} s"}
 
     if rank == 0:
         it = [s["iterations"] for s in stats]
@@ -805,7 +868,8 @@ def main():
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
             "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "large": large, "apply_sweep": sweep, "solve_32x4": solve32, "paper_solver_table": invtab,
-            "fma_peak_TFLOP_s": {"fp64": fp64_peak, "fp32": fp32_peak}, "batch": batch, "kernels": kernels, "e2e": e2e, "roofline": roofline, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
+            "fma_peak_TFLOP_s": {"fp64": fp64_peak, "fp32": fp32_peak}, "batch": batch, "kernels": kernels, "kernels_full_launch": kernels_full, "e2e": e2e, "roofline": roofline,
+            "roofline_full_launch": roofline_full, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),
             "hmc_traj_per_s": None if hmc is None else {
                 "single_mixed": hmc["single_mixed"]["traj_per_s"], "single_fp64": hmc["single_fp64"]["traj_per_s"],

@@ -247,6 +247,17 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   auto issue_chunk = [&](cudaStream_t q) -> cudaError_t {
     cudaError_t e2;
     if (nbranch > 1 && gsz < nrhs) {
+      // The kernel probe times launches one at a time: the same per-group
+      // launches (each group with its own scalar and reliable-update kernels)
+      // in the same order, all on q, so that every launch of a class is
+      // bracketed alone and the class counts are those of the timed solve.
+      if (g_probe.active) {
+        for (int r0 = 0; r0 < nrhs; r0 += gsz) {
+          const int ng = nrhs - r0 < gsz ? nrhs - r0 : gsz;
+          if ((e2 = issue_group_chunk(r0, ng, q)) != cudaSuccess) return e2;
+        }
+        return cudaSuccess;
+      }
       // fork the branch streams off q, deal the groups round robin, join
       const int nb = nbranch;
       if ((e2 = cudaEventRecord(c->ev_fork, q)) != cudaSuccess) return e2;
@@ -400,8 +411,6 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     }
   }
 
-  // the kernel probe times launches one by one: no concurrent branches then
-  if (g_probe.active) nbranch = 1;
 
   // Graph mode: the whole chunk loop is one CUDA graph whose body sits in a
   // WHILE conditional node; a one-thread kernel at the end of the body keeps

@@ -1,8 +1,14 @@
-"""Apply one operator of the library repeatedly, for profiling a pass in isolation.
+"""Apply one operator of the library repeatedly, or run a bounded mixed CG
+solve, for profiling a pass in isolation.
 
 Usage (a CUDA device and the built libwz.so are required):
 
     python -m paper_1005_3276_gb300.profile_apply --dims 16 16 16 16 --nrhs 16 --op MdagM --dtype c64 --reps 3
+    WZ_NO_GRAPHS=1 python -m paper_1005_3276_gb300.profile_apply --nrhs 12 --solve-iters 24
+
+With --solve-iters N the script runs one mixed-precision solve of (M^dag M) x = b
+for the right-hand sides, stopped after N iterations (the CG passes of the
+solver; WZ_NO_GRAPHS=1 makes them separate launches a profiler can capture).
 
 Fields are seeded synthetic inputs (phi Gaussian sigma 0.5, right-hand sides
 unit complex Gaussian), m = 0.05, g = 0.3.  Each repetition is one call of the
@@ -21,6 +27,7 @@ def main():
     ap.add_argument("--op", default="MdagM")
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--solve-iters", type=int, default=0, help="run a mixed CG solve stopped after N iterations")
     args = ap.parse_args()
 
     import torch
@@ -32,6 +39,14 @@ def main():
     dt = torch.complex64 if args.dtype == "c64" else torch.complex128
     lat = wz.Lattice(dims, m=0.05, g=0.3)
     lat.set_phi(torch.from_numpy(synth.scalar_field(dims, 0.5, 0)).cuda())
+    if args.solve_iters > 0:
+        b = torch.from_numpy(synth.spinor_rhs(args.nrhs, dims, 1)).cuda()
+        xs = torch.zeros_like(b)
+        rc, st, _ = lat.solve(b, xs, tol=1e-10, maxiter=args.solve_iters, mixed=True, raise_on_nonconvergence=False)
+        torch.cuda.synchronize()
+        print(f"solve {dims} x {args.nrhs}: {st['iterations']} iterations, status {rc}")
+        lat.close()
+        return
     x = torch.from_numpy(synth.spinor_rhs(args.nrhs, dims, 1)).to(dt).cuda()
     y = torch.empty_like(x)
     stream = torch.cuda.current_stream()

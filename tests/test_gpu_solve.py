@@ -111,6 +111,22 @@ def test_solve_other_shapes(wz, dims):
     assert oracle_residual(P, phi, b, x) <= TOL
 
 
+@pytest.mark.parametrize("pc", [False, True])
+def test_solve_paper_lattice_32x64(wz, pc):
+    """The paper's largest lattice, 32^3 x 64, at its solver-table couplings
+    (m = 1, g = 0.2): mixed solve to 1e-10, residual recomputed by the oracle."""
+    dims = (64, 32, 32, 32)
+    P = oracle.Params(dims=dims, m=1.0, g=0.2)
+    phi = synth.scalar_field(dims, 0.5, 0)
+    b = synth.spinor_rhs(1, dims, 1)
+    lat = wz.Lattice(dims, m=P.m, g=P.g)
+    lat.set_phi(phi)
+    x = np.zeros_like(b)
+    rc, st, _ = lat.solve(b, x, tol=TOL, mixed=True, pc=pc)
+    print("32^3 x 64", "PC" if pc else "no PC", st["iterations"], "iterations")
+    assert oracle_residual(P, phi, b, x) <= TOL
+
+
 @pytest.mark.parametrize("mixed", [True, False])
 def test_precision_workload_16(wz, mixed):
     """16^4, m = 0.05, g = 0.3, 12 RHS to 1e-10 true residual (FP64 and mixed);

@@ -674,8 +674,9 @@ def main():
                  "est_full_trajectory_s": t_traj * (2 * lw.extra["nsteps"] + 1) / max(1, tst["force_evals"]),
                  "aux_vev": [F.real, F.imag], "aux_s": t_aux,
                  "ward_s": t_ward, "ward_cg_iterations_max": wst["iterations"],
-                 "ward_R_trace": [float(np.trace(WR).real), float(np.trace(WR).imag)],
-                 "ward_L_trace": [float(np.trace(WL).real), float(np.trace(WL).imag)],
+                 # the [0][1] element of both sides (C has a zero diagonal, so tr W_L vanishes)
+                 "ward_R_01": [float(WR[0, 1].real), float(WR[0, 1].imag)],
+                 "ward_L_01": [float(WL[0, 1].real), float(WL[0, 1].imag)],
                  "supercurrent_s": t_sc, "supercurrent_cg_iterations_max": sst["iterations"],
                  "supercurrent_R0_mu0_dx1_dy0_trace": [float(np.trace(Rsc[0, 0, 1, 0]).real),
                                                        float(np.trace(Rsc[0, 0, 1, 0]).imag)]}

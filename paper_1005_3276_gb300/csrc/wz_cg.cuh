@@ -161,8 +161,20 @@ template <typename R, int L, int MODE, bool PC> struct CGSmem {
                 "bulk copies move multiples of 16 bytes");
 };
 
+// Blocks per SM a CG pass is compiled for (its register budget): FP32 passes
+// WZ_XY_MINB 256-thread blocks' worth of threads, but no more blocks than the
+// pass's shared memory lets reside (228 KB per SM, 1 KB reserved a block), so
+// that no pass is held to fewer registers than its occupancy allows; FP64
+// passes (the FP64 solver and the reliable updates) two 256-thread blocks'
+// worth (128 registers at 128 threads), one for 32-point lines (255).
+template <typename R, int L, int MODE, bool PC> struct CGMinBlocks {
+  static constexpr int by_threads = ((sizeof(R) == 8 ? (L >= 32 ? 1 : 2) : WZ_XY_MINB) * 256) / XYShape<L>::THREADS;
+  static constexpr int by_smem = (int)((228u * 1024u) / (CGSmem<R, L, MODE, PC>::total + 1024u));
+  static constexpr int value = by_threads < by_smem ? by_threads : (by_smem > 0 ? by_smem : 1);
+};
+
 template <typename R, typename LO, int L, int MODE, bool PC>
-__global__ void __launch_bounds__(XYShape<L>::THREADS, (WZ_XY_MINB * 256) / XYShape<L>::THREADS)
+__global__ void __launch_bounds__(XYShape<L>::THREADS, (CGMinBlocks<R, L, MODE, PC>::value))
 xy_cg(CGArgs<R, LO> a) {
   using S = XYShape<L>;
   using H = XYPhase<R, L>;

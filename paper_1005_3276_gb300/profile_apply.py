@@ -42,9 +42,21 @@ def main():
     if args.solve_iters > 0:
         b = torch.from_numpy(synth.spinor_rhs(args.nrhs, dims, 1)).cuda()
         xs = torch.zeros_like(b)
-        rc, st, _ = lat.solve(b, xs, tol=1e-10, maxiter=args.solve_iters, mixed=True, raise_on_nonconvergence=False)
-        torch.cuda.synchronize()
-        print(f"solve {dims} x {args.nrhs}: {st['iterations']} iterations, status {rc}")
+        stream = torch.cuda.current_stream()
+        times = []
+        for _ in range(max(1, args.reps)):
+            xs.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            rc, st, _ = lat.solve(b, xs, tol=1e-10, maxiter=args.solve_iters, mixed=True,
+                                  raise_on_nonconvergence=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        n = st["total_iterations"] + st["reliable_updates"]
+        print(f"solve {dims} x {args.nrhs}: {st['iterations']} iterations, status {rc}, "
+              f"{min(times):.2f} ms (best of {len(times)}), {n / (min(times) / 1000.0):.0f} applies/s")
         lat.close()
         return
     x = torch.from_numpy(synth.spinor_rhs(args.nrhs, dims, 1)).to(dt).cuda()

@@ -503,7 +503,9 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st, const 
     key.b_solver = c->ws_solver.bytes;
     key.b_apply = c->ws_apply.bytes;
     TrajGraph& T = c->traj_graph;
-    if (!T.exec || memcmp(&key, &T.key, sizeof(key)) != 0) {
+    // a capture that fails with the solvers' dependent launches is repeated
+    // once with plain launches (and the context keeps to them)
+    for (int attempt = 0; attempt < 2 && (!T.exec || memcmp(&key, &T.key, sizeof(key)) != 0); ++attempt) {
       T.release();
       WZ_CUDA_TRY(c, cudaStreamSynchronize(s));
       const unsigned long long l0 = tl_launches;
@@ -524,15 +526,28 @@ int trajectory_impl(wz_ctx* c, const wz_hmc_params* h, wz_traj_stats* st, const 
       g_launches -= T.outer_launches;
       tl_launches = l0;
       if (e != cudaSuccess) return cuda_error(c, e, "trajectory capture");
-      if (rc2) {
-        if (gr) cudaGraphDestroy(gr);
-        return rc2;
+      cudaError_t ei = cudaErrorUnknown;
+      if (!rc2 && ee == cudaSuccess) {
+        T.graph = gr;
+        gr = nullptr;
+        ei = cudaGraphInstantiate(&T.exec, T.graph, 0);
+        if (ei == cudaSuccess) {
+          T.force_evals = nf;
+          T.key = key;
+          break;
+        }
       }
+      if (gr) cudaGraphDestroy(gr);
+      if (attempt == 0 && !c->pdl_capture_failed) {
+        cudaGetLastError();
+        T.release();
+        c->pdl_capture_failed = true;
+        c->err.clear();
+        continue;
+      }
+      if (rc2) return rc2;
       if (ee != cudaSuccess) return cuda_error(c, ee, "trajectory cudaStreamEndCapture");
-      T.graph = gr;
-      WZ_CUDA_TRY(c, cudaGraphInstantiate(&T.exec, T.graph, 0));
-      T.force_evals = nf;
-      T.key = key;
+      return cuda_error(c, ei, "cudaGraphInstantiate (trajectory)");
     }
     WZ_CUDA_TRY(c, cudaGraphLaunch(T.exec, s));
     nf = T.force_evals;

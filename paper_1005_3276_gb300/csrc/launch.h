@@ -2,6 +2,8 @@
 // instantiations in their own translation units (kern_L*.cu, zt_*.cu), so the
 // host code here only dispatches on the run-time extent.
 #pragma once
+#include <utility>
+
 #include "wz_ctx.h"
 #include "wz_hmc.cuh"
 #include "wz_probe.h"
@@ -13,6 +15,29 @@
 namespace wz {
 
 enum { FK_FORCE = 0, FK_BOSON_FWD = 1, FK_BOSON_INV = 2 };
+
+// Launch k on st, with programmatic stream serialization when pdl is set (the
+// kernel may then be scheduled while its predecessor on st finishes; it waits
+// for it in pdl_wait before touching memory).
+template <typename... KArgs, typename... Args>
+static cudaError_t launch_k(bool pdl, void (*k)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args&&... args) {
+  if (!pdl) {
+    k<<<grid, block, smem, st>>>(std::forward<Args>(args)...);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k, std::forward<Args>(args)...);
+}
 
 template <typename Kern>
 static cudaError_t set_smem(Kern k, size_t bytes) {

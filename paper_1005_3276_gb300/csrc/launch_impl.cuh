@@ -132,15 +132,17 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
   }
   const long ntot = (long)nrhs * a.ntiles;
   if (ntot == 0) return cudaSuccess;
-  // persistent grid: at most the blocks resident on the device, balanced so
-  // that every block takes the same number of tiles (ceil(ntot / grid))
+  // persistent grid: at most the blocks resident on the device (fewer when the
+  // caller asks for at least a.tpb tiles a block), balanced so that every
+  // block takes the same number of tiles (ceil(ntot / grid))
   static ResidentBlocks resident;
   int gmax = 0;
   {
     cudaError_t e = resident.get(zt_pass<R, NZ, NT, MUL>, S::THREADS, smem, &gmax);
     if (e != cudaSuccess) return e;
   }
-  const long per = (ntot + gmax - 1) / gmax;
+  long per = (ntot + gmax - 1) / gmax;
+  if (a.tpb > per) per = a.tpb;
   const long grid = (ntot + per - 1) / per;
   // the map covers right-hand sides 0 .. rhs0 + nrhs - 1 of A; the last one is reused
   const R* t0 = (MUL == ZT_DSLASH || MUL == ZT_GRAD || MUL == ZT_OVERLAP) ? a.hV : (MUL == ZT_SCALAR ? a.d2sV : a.hdV);
@@ -180,8 +182,8 @@ static cudaError_t launch_zt_t(const ZTArgs<R>& a, int nrhs, cudaStream_t st) {
     b.ntot = (int)ntot;
     b.blk_count = cnt;
     b.probe_inc = (unsigned long long)bytes;
-    zt_pass<R, NZ, NT, MUL><<<(unsigned)grid, S::THREADS, smem, st>>>(b, tm, tm0, tm1);
-    return cudaGetLastError();
+    return launch_k(b.pdl != 0, zt_pass<R, NZ, NT, MUL>, dim3((unsigned)grid), dim3(S::THREADS), smem, st, b, tm,
+                    tm0, tm1);
   });
 }
 
@@ -228,8 +230,7 @@ static cudaError_t launch_cg_t(const CGArgs<R, LO>& a, int nrhs, cudaStream_t st
     CGArgs<R, LO> b = a;
     b.blk_count = cnt;
     b.probe_inc = (unsigned long long)blk_bytes;
-    xy_cg<R, LO, L, MODE, PC><<<grid, S::THREADS, smem, st>>>(b);
-    return cudaGetLastError();
+    return launch_k(b.pdl != 0, xy_cg<R, LO, L, MODE, PC>, grid, dim3(S::THREADS), smem, st, b);
   });
 }
 

@@ -170,6 +170,18 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
   // branches of the graph), each group with its own scalar and reliable-update
   // kernels, so that the passes of one group overlap those of the others.
   int nbranch = 1;
+  // Programmatic dependent launch of the chain's kernels (each kernel's launch
+  // and block set-up overlap the tail of the one before it on its stream);
+  // chosen with the groups, never while the probe brackets single launches.
+  bool pdl = false;
+  auto set_pdl = [&](bool on) {
+    pdl = on && !g_probe.active;
+    ga.pdl = ra.pdl = z1.pdl = z2.pdl = y1.pdl = y2.pdl = pdl ? 1 : 0;
+  };
+  // Tiles per block of the FP32 zt passes (their persistent grid: 0 starts as
+  // many blocks as are resident; k > 0 at most ceil(tiles / k) blocks, which
+  // leaves SMs to the concurrent groups).
+  auto set_ztpb = [&](int k) { z1.tpb = z2.tpb = k; };
 
   // iteration counters of the chunks (off while the tuner times candidates)
   unsigned long long* cnt = c->counters;
@@ -202,9 +214,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
       a5.part_out = part5;
       WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, ng, q));
       count_launch();
-      cg_scalar_iter<<<ng, 32, 0, q>>>(st + r0, part5 + (long)r0 * nblk, part3 + (long)r0 * nblk, nblk, delta2,
-                                       maxiter, cnt);
-      WZ_Q(cudaGetLastError());
+      WZ_Q(launch_k(pdl, cg_scalar_iter, dim3(ng), dim3(32), 0, q, st + r0, part5 + (long)r0 * nblk,
+                    part3 + (long)r0 * nblk, nblk, delta2, maxiter, cnt));
     }
     CGArgs<double, RI> u1 = ra;
     u1.rhs0 = r0;
@@ -228,6 +239,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     u3.TZ = TZ;
     u3.gate_ru = 1;
     u3.rhs0 = r0;
+    u3.pdl = ra.pdl;
     WZ_Q(launch_cg<double, double>(L, pc, CG_P3, u3, ng, q));
     ZTArgs<double> w2 = y2;
     w2.rhs0 = r0;
@@ -237,8 +249,8 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     u5.part_out = partR;
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P5, u5, ng, q));
     count_launch();
-    cg_scalar_ru<<<ng, 32, 0, q>>>(st + r0, partR + (long)r0 * nblk, nblk, maxiter, cnt);
-    WZ_Q(cudaGetLastError());
+    WZ_Q(launch_k(pdl, cg_scalar_ru, dim3(ng), dim3(32), 0, q, st + r0, partR + (long)r0 * nblk, nblk, maxiter,
+                  cnt));
 #undef WZ_Q
     return cudaSuccess;
   };
@@ -303,8 +315,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
         WZ_Q(launch_cg<RI, RI>(L, pc, CG_P5, a5, ng, q));
       }
       count_launch();
-      cg_scalar_iter<<<nrhs, 32, 0, q>>>(st, part5, part3, nblk, delta2, maxiter, cnt);
-      WZ_Q(cudaGetLastError());
+      WZ_Q(launch_k(pdl, cg_scalar_iter, dim3(nrhs), dim3(32), 0, q, st, part5, part3, nblk, delta2, maxiter, cnt));
     }
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P1, ra, nrhs, q));
     WZ_Q(launch_zt<double>(c->Z, c->T, mul1, y1, nrhs, q));
@@ -323,98 +334,146 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     r3.nblk = nblk;
     r3.TZ = TZ;
     r3.gate_ru = 1;
+    r3.pdl = ra.pdl;
     WZ_Q(launch_cg<double, double>(L, pc, CG_P3, r3, nrhs, q));
     WZ_Q(launch_zt<double>(c->Z, c->T, mul2, y2, nrhs, q));
     CGArgs<double, RI> r5 = ra;
     r5.part_out = partR;
     WZ_Q(launch_cg<double, RI>(L, pc, RU_P5, r5, nrhs, q));
     count_launch();
-    cg_scalar_ru<<<nrhs, 32, 0, q>>>(st, partR, nblk, maxiter, cnt);
-    WZ_Q(cudaGetLastError());
+    WZ_Q(launch_k(pdl, cg_scalar_ru, dim3(nrhs), dim3(32), 0, q, st, partR, nblk, maxiter, cnt));
 #undef WZ_Q
     return cudaSuccess;
   };
 
-  // Autotune the RHS group size and the branch count once per solve shape: for
-  // each candidate, re-initialise and time three chunks (24 iterations) with CUDA
-  // events, twice, keeping the better round.  The cache holds 8 * gsz + nbranch.
+  // Autotune the RHS group size, the branch count, dependent launch and the zt
+  // passes' tiles per block once per solve shape: for each candidate,
+  // re-initialise and time three chunks (24 iterations) with CUDA events,
+  // twice, keeping the better round.  The first three are searched jointly
+  // (with the zt grid at the resident blocks), the tiles per block for the
+  // winner.
   {
+    struct Choice {
+      int g, nb, pdl, tpb;
+    };
     static std::mutex mu;
-    static std::map<std::vector<long>, int> cache;
+    static std::map<std::vector<long>, Choice> cache;
     const std::vector<long> tkey{(long)sizeof(RI), (long)pc, (long)c->T, (long)c->Z, (long)c->X, (long)nrhs,
                                  (long)c->nm};
-    int found = 0;
+    bool found = false;
+    Choice fc{};
     {
       std::lock_guard<std::mutex> lk(mu);
       auto it = cache.find(tkey);
-      if (it != cache.end()) found = it->second;
+      if (it != cache.end()) {
+        found = true;
+        fc = it->second;
+      }
     }
     const char* forced = getenv("WZ_RHS_GROUP");  // a fixed group size overrides the tuner
     const char* forced_b = getenv("WZ_RHS_BRANCHES");
+    const char* forced_pdl = getenv("WZ_PDL");     // 0 or 1 overrides the tuner's dependent-launch choice
+    const char* forced_tpb = getenv("WZ_ZT_TPB");  // zt tiles per block (0: resident blocks)
+    const bool pdl_forced = forced_pdl && (forced_pdl[0] == '0' || forced_pdl[0] == '1');
+    const bool tpb_forced = forced_tpb && forced_tpb[0] >= '0' && forced_tpb[0] <= '9';
+    // dependent launch by default (a solve that cannot be timed), unless a
+    // graph capture with it has failed on this context
+    bool pdl_pick = pdl_forced ? forced_pdl[0] == '1' : !c->pdl_capture_failed;
+    int tpb_pick = tpb_forced ? atoi(forced_tpb) : 0;
     if (forced && atoi(forced) > 0) {
       gsz = atoi(forced) < nrhs ? atoi(forced) : nrhs;
       nbranch = forced_b ? atoi(forced_b) : 1;
       nbranch = nbranch < 1 ? 1 : (nbranch > wz_ctx::kMaxBranches ? wz_ctx::kMaxBranches : nbranch);
     } else if (found) {
-      gsz = found / 8;
-      nbranch = found % 8;
+      gsz = fc.g;
+      nbranch = fc.nb;
+      if (!pdl_forced) pdl_pick = fc.pdl != 0 && !c->pdl_capture_failed;
+      if (!tpb_forced) tpb_pick = fc.tpb;
     } else if (inline_capture && nrhs >= 8) {
       // no timing inside a capture: four groups on four branches (the choice the
       // tuner makes for 12 right-hand sides at 16^4)
       gsz = (nrhs + 3) / 4;
       nbranch = (nrhs + gsz - 1) / gsz;
-    } else if (nrhs > 1 && !inline_capture && !g_probe.active) {
-      std::vector<std::pair<int, int>> cand;
+    } else if (!inline_capture && !g_probe.active) {
+      std::vector<Choice> cand;
       for (int d : {1, 2, 3, 4, 6, 8})
         if (nrhs / d >= 1) {
           const int g = (nrhs + d - 1) / d;
           const int ngroups = (nrhs + g - 1) / g;
           for (int nb = 1; nb <= (ngroups < wz_ctx::kMaxBranches ? ngroups : wz_ctx::kMaxBranches); ++nb)
-            if (std::find(cand.begin(), cand.end(), std::make_pair(g, nb)) == cand.end()) cand.emplace_back(g, nb);
+            for (int pd = 0; pd < 2; ++pd) {
+              if (pdl_forced && pd != (pdl_pick ? 1 : 0)) continue;
+              bool dup = false;
+              for (const Choice& k : cand) dup |= (k.g == g && k.nb == nb && k.pdl == pd);
+              if (!dup) cand.push_back(Choice{g, nb, pd, tpb_pick});
+            }
         }
       cudaEvent_t e0, e1;
       cnt = nullptr;
       WZ_RUN(cudaEventCreate(&e0));
       WZ_RUN(cudaEventCreate(&e1));
-      float best = 1e30f;
-      int bestg = nrhs, bestb = 1;
-      for (const auto& cb : cand) {
-        gsz = cb.first;
-        nbranch = cb.second;
-        WZ_RUN(issue_chunk(s));  // warm-up on whatever state the recursion is in
+      auto time_choice = [&](const Choice& cb, float* out_ms) -> cudaError_t {
+        cudaError_t e2;
+        gsz = cb.g;
+        nbranch = cb.nb;
+        set_pdl(cb.pdl != 0);
+        set_ztpb(cb.tpb);
+        if ((e2 = issue_chunk(s)) != cudaSuccess) return e2;  // warm-up on whatever state the recursion is in
         // the better of two timed rounds of three chunks (candidates a few
         // percent apart are otherwise ordered by noise)
         float ms = 1e30f;
         for (int round = 0; round < 2; ++round) {
-          WZ_RUN(cudaEventRecord(e0, s));
-          for (int rep = 0; rep < 3; ++rep) WZ_RUN(issue_chunk(s));
-          WZ_RUN(cudaEventRecord(e1, s));
-          WZ_RUN(cudaEventSynchronize(e1));
+          if ((e2 = cudaEventRecord(e0, s)) != cudaSuccess) return e2;
+          for (int rep = 0; rep < 3; ++rep)
+            if ((e2 = issue_chunk(s)) != cudaSuccess) return e2;
+          if ((e2 = cudaEventRecord(e1, s)) != cudaSuccess) return e2;
+          if ((e2 = cudaEventSynchronize(e1)) != cudaSuccess) return e2;
           float t = 0.f;
-          WZ_RUN(cudaEventElapsedTime(&t, e0, e1));
+          if ((e2 = cudaEventElapsedTime(&t, e0, e1)) != cudaSuccess) return e2;
           ms = t < ms ? t : ms;
         }
-        if (ms < best) {
-          best = ms;
-          bestg = cb.first;
-          bestb = cb.second;
-        }
+        *out_ms = ms;
         // back to the initial state of the solve
-        WZ_RUN(cudaMemsetAsync(xs, 0, W.field64, s));
+        if ((e2 = cudaMemsetAsync(xs, 0, W.field64, s)) != cudaSuccess) return e2;
         count_launch(2);
         cg_init<RI><<<dim3(64, nrhs), 256, 0, s>>>(bs, r, xlo, p, n_per_rhs, partR, 64);
-        WZ_RUN(cudaGetLastError());
+        if ((e2 = cudaGetLastError()) != cudaSuccess) return e2;
         cg_scalar_init<<<nrhs, 32, 0, s>>>(st, partR, 64, tol * tol, sh);
-        WZ_RUN(cudaGetLastError());
+        return cudaGetLastError();
+      };
+      float best = 1e30f;
+      Choice bestc{nrhs, 1, 0, tpb_pick};
+      for (const Choice& cb : cand) {
+        float ms = 0.f;
+        WZ_RUN(time_choice(cb, &ms));
+        if (ms < best) {
+          best = ms;
+          bestc = cb;
+        }
       }
+      if (!tpb_forced)
+        for (int k : {2, 4}) {
+          Choice cb = bestc;
+          cb.tpb = k;
+          float ms = 0.f;
+          WZ_RUN(time_choice(cb, &ms));
+          if (ms < best) {
+            best = ms;
+            bestc = cb;
+          }
+        }
       cudaEventDestroy(e0);
       cudaEventDestroy(e1);
       cnt = c->counters;
-      gsz = bestg;
-      nbranch = bestb;
+      gsz = bestc.g;
+      nbranch = bestc.nb;
+      pdl_pick = bestc.pdl != 0;
+      tpb_pick = bestc.tpb;
       std::lock_guard<std::mutex> lk(mu);
-      cache[tkey] = 8 * gsz + nbranch;
+      cache[tkey] = bestc;
     }
+    set_pdl(pdl_pick);
+    set_ztpb(tpb_pick);
   }
 
 
@@ -481,7 +540,11 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     key.phi32 = c->phi32;
     key.gsz = gsz;
     key.nbranch = nbranch;
-    if (!G.exec || memcmp(&key, &G.key, sizeof(key)) != 0) {
+    key.pdl = pdl ? 1 : 0;
+    key.tpb = z1.tpb;
+    // a capture or instantiation that fails with dependent launches is
+    // repeated once with plain launches (and the context keeps to them)
+    for (int attempt = 0; attempt < 2 && (!G.exec || memcmp(&key, &G.key, sizeof(key)) != 0); ++attempt) {
       G.release();
       WZ_CUDA_TRY(c, cudaGraphCreate(&G.graph, 0));
       cudaGraphConditionalHandle h;
@@ -508,10 +571,22 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
       tl_launches = l0;
       cudaGraph_t captured = nullptr;
       cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &captured);
+      cudaError_t ei = (ce == cudaSuccess && ee == cudaSuccess) ? cudaGraphInstantiate(&G.exec, G.graph, 0) : ce;
+      if (ce == cudaSuccess && ee == cudaSuccess && ei == cudaSuccess) {
+        G.key = key;
+        break;
+      }
+      if (pdl && attempt == 0) {
+        cudaGetLastError();
+        G.release();
+        c->pdl_capture_failed = true;
+        set_pdl(false);
+        key.pdl = 0;
+        continue;
+      }
       if (ce != cudaSuccess) return cuda_error(c, ce, "solver graph capture");
       if (ee != cudaSuccess) return cuda_error(c, ee, "cudaStreamEndCapture");
-      WZ_CUDA_TRY(c, cudaGraphInstantiate(&G.exec, G.graph, 0));
-      G.key = key;
+      return cuda_error(c, ei, "cudaGraphInstantiate (solver)");
     }
   }
 

@@ -98,6 +98,7 @@ template <typename R, typename LO> struct CGArgs {
   int rhs0;             // first right-hand side of this launch (blockIdx.y counts from it)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one block moves
+  int pdl;              // host side: launch with programmatic stream serialization
 };
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -192,16 +193,25 @@ xy_cg(CGArgs<R, LO> a) {
 
   const int rhs = blockIdx.y + a.rhs0;
   RhsState* st = a.st + rhs;
-  if (!(a.gate_ru ? st->ru : st->run)) return;  // whole block, before any barrier
-  const double shift = st->shift;
+  // Dependent launch: a pass waits for its predecessor (pdl_wait) before it
+  // touches what that kernel writes, and every block waits before it leaves,
+  // so that a grid completes only after the grid before it has.  The staged
+  // FP32 passes issue the copies of the operands written two or more launches
+  // back before that wait, so that they overlap the predecessor's tail: P1
+  // (after the scalar kernel, which writes only the per-RHS state) r, p and x;
+  // P3 and P5 (after a zt pass, which writes only A) p, C, r and phi.  Whether
+  // to issue them early is decided from the gate as read before the wait (P1:
+  // from whether the system is still active); the gate that counts is read
+  // after the wait, and a block whose system does not run lets any copies it
+  // issued land (bounded) and leaves.
+  if constexpr (!STAGE) {
+    pdl_wait();
+    pdl_trigger();
+    if (!(a.gate_ru ? st->ru : st->run)) return;  // whole block, before any barrier
+  }
 
   // staged operands: one bulk copy per operand for the block's consecutive planes
-  bool stage_x = false, stage_p = false;
   if constexpr (STAGE) {
-    if constexpr (MODE == CG_P1) {
-      stage_x = st->alpha != 0.0;
-      stage_p = stage_x || st->beta != 0.0;
-    }
     // bulk copies need 16-byte aligned shared and global addresses: checked,
     // the right-hand side is marked failed and no copy is issued otherwise
     const bool misaligned = ((smem_u32(sm) | smem_u32(stg) | smem_u32(sphi)) & 15u) != 0 ||
@@ -209,6 +219,8 @@ xy_cg(CGArgs<R, LO> a) {
                               (unsigned long long)a.A | (unsigned long long)a.Cb | (unsigned long long)a.phi) &
                              15ull) != 0;
     if (__syncthreads_or(misaligned)) {
+      pdl_wait();
+      pdl_trigger();
       if (threadIdx.x == 0) {
         st->status = WZ_ECUDA;
         st->run = 0;
@@ -217,24 +229,18 @@ xy_cg(CGArgs<R, LO> a) {
       }
       return;
     }
-    if (threadIdx.x == 0) {
-      mbar_init(&bars[0], 1);
-      mbar_init(&bars[1], 1);
-      mbar_fence_init();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int nlive = min(S::PPC, a.TZ - (int)blockIdx.x * S::PPC);
-      const unsigned nb = (unsigned)(nlive * SM::plane_bytes);
-      const long off0 = ((long)rhs * a.TZ + (long)blockIdx.x * S::PPC) * PE;
+    const int nlive = min(S::PPC, a.TZ - (int)blockIdx.x * S::PPC);
+    const unsigned nb = (unsigned)(nlive * SM::plane_bytes);
+    const long off0 = ((long)rhs * a.TZ + (long)blockIdx.x * S::PPC) * PE;
+    // thread 0: the copies of the operands that do not come from the predecessor
+    auto issue_operands = [&]() {
       if constexpr (MODE == CG_P1) {
-        mbar_arrive_expect_tx(&bars[1], nb * (1u + (stage_p ? 1u : 0u) + (stage_x ? 1u : 0u)));
+        // p and x also in the first iteration (zeros), when alpha = beta = 0
+        mbar_arrive_expect_tx(&bars[1], 3u * nb);
         bulk_g2s(stg, a.r + off0, nb, &bars[1]);
-        if (stage_p) bulk_g2s(stg + S::PPC * PE, a.p + off0, nb, &bars[1]);
-        if (stage_x) bulk_g2s(sm, a.x + off0, nb, &bars[1]);
+        bulk_g2s(stg + S::PPC * PE, a.p + off0, nb, &bars[1]);
+        bulk_g2s(sm, a.x + off0, nb, &bars[1]);
       } else {
-        mbar_arrive_expect_tx(&bars[0], nb);
-        bulk_g2s(sm, a.A + off0, nb, &bars[0]);
         // phi planes of the block's member (the planes are consecutive within it)
         const unsigned nphi = SM::STAGE_PHI ? (unsigned)(nlive * SM::phi_plane_bytes) : 0u;
         const long phi0 = ((long)(rhs / a.rpm) * a.TZ + (long)blockIdx.x * S::PPC) * (L * L);
@@ -248,8 +254,32 @@ xy_cg(CGArgs<R, LO> a) {
         }
         if constexpr (SM::STAGE_PHI) bulk_g2s(sphi, a.phi + phi0, nphi, &bars[1]);
       }
+    };
+    const bool hint = threadIdx.x == 0 && (MODE == CG_P1 ? *(volatile const int*)&st->active != 0
+                                                         : *(volatile const int*)(a.gate_ru ? &st->ru : &st->run) != 0);
+    if (threadIdx.x == 0) {
+      mbar_init(&bars[0], 1);
+      mbar_init(&bars[1], 1);
+      mbar_fence_init();
+    }
+    const bool early = __syncthreads_or(hint);  // also publishes the initialised barriers
+    if (threadIdx.x == 0 && early) issue_operands();
+    pdl_wait();
+    pdl_trigger();
+    if (!__syncthreads_or((a.gate_ru ? st->ru : st->run) != 0)) {
+      if (early) mbar_wait_bounded(&bars[1], 0);
+      return;
+    }
+    if (threadIdx.x == 0) {
+      if (!early) issue_operands();
+      if constexpr (MODE != CG_P1) {
+        // the momentum input A is the predecessor's output
+        mbar_arrive_expect_tx(&bars[0], nb);
+        bulk_g2s(sm, a.A + off0, nb, &bars[0]);
+      }
     }
   }
+  const double shift = st->shift;  // set before the iteration loop
   // a staged wait that ran out: mark this right-hand side failed, let the
   // copies in flight land (bounded) and leave as a whole block
   auto stage_failed = [&](bool ok) -> bool {
@@ -511,6 +541,8 @@ static __global__ void cg_scalar_init(RhsState* st, const double* part, int nblk
 static __global__ void cg_scalar_iter(RhsState* st, const double* part, const double* part_pAp, int nblk,
                                       double delta2, int maxiter, unsigned long long* counters) {
   RhsState* s = st + blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (!s->run) return;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
   // the alpha P5 used (the same sum, in the same order): pending for the next P1
@@ -539,6 +571,8 @@ static __global__ void cg_scalar_iter(RhsState* st, const double* part, const do
 static __global__ void cg_scalar_ru(RhsState* st, const double* part, int nblk, int maxiter,
                                     unsigned long long* counters) {
   RhsState* s = st + blockIdx.x;
+  pdl_wait();
+  pdl_trigger();
   if (!s->ru) return;
   const double t = sum_partials(part + (long)blockIdx.x * nblk, nblk);
   if (threadIdx.x == 0) {

@@ -80,6 +80,8 @@ struct SolverGraphKey {
   const void* phi32;
   int gsz;      // right-hand sides per group
   int nbranch;  // streams the groups alternate between
+  int pdl;      // kernels launched with programmatic stream serialization
+  int tpb;      // tiles per block of the FP32 zt passes (0: resident blocks)
 };
 struct SolverGraph {
   SolverGraphKey key{};
@@ -155,6 +157,7 @@ struct wz_ctx {
   void* host_pinned = nullptr;
   // solver graphs and their capture stream
   bool use_graphs = true;
+  bool pdl_capture_failed = false;             // a graph capture with dependent launches failed: plain launches
   cudaStream_t cap_stream = nullptr;
   cudaStream_t cap_stream2 = nullptr;          // body of solver loops inside a trajectory capture
   // extra branches of a solver chunk (RHS groups on concurrent streams)

@@ -30,6 +30,20 @@
 
 namespace wz {
 
+// ----------------------------------------------------------------------------- dependent launch
+// Programmatic dependent launch (sm_90 and later).  A kernel launched with
+// programmatic stream serialization may be scheduled while its predecessor on
+// the stream is still running.  pdl_wait() returns once every prerequisite grid
+// has completed and its memory writes are visible (at once for a plain launch);
+// pdl_trigger() lets the successor be scheduled as soon as every block of this
+// grid has called it or exited.  The kernels of the solver chain call both at
+// entry, before their first global-memory access: a successor that starts
+// early overlaps only its launch and block set-up with this grid's tail, and a
+// grid triggers only after its own wait, so the grid before the predecessor
+// has completed whenever a successor starts.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ----------------------------------------------------------------------------- site terms
 // Y      = (m + c g phi) P_+ + (m^* + c g^* phi^*) P_-       (Eq. fmat)
 // Y_int  =      c g phi  P_+ +        c g^* phi^*  P_-
@@ -352,6 +366,8 @@ template <typename R> struct ZTArgs {
   int ntot;            // tiles of this launch: (right-hand sides of the launch) x ntiles (set by the launcher)
   unsigned long long* blk_count;  // probe: byte counter (may be null)
   unsigned long long probe_inc;   // probe: algorithmic bytes one tile moves
+  int pdl;             // host side: launch with programmatic stream serialization
+  int tpb;             // host side: tiles per block at least (0: as many blocks as are resident)
 };
 
 // Columns per tile: C0 columns (8 C0 B FP32 / 16 C0 B FP64 contiguous per
@@ -695,6 +711,8 @@ zt_pass(ZTArgs<R> a, const __grid_constant__ CUtensorMap tmA, const __grid_const
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(smem_raw + ZS::bar_off);
   const int tid = threadIdx.x;
   const int G = gridDim.x;
+  pdl_wait();  // the gates and the tiles are the predecessor's output
+  pdl_trigger();
 
   // the next tile of this block at or after q whose right-hand side runs
   // (the gates are not written while the pass runs: every thread agrees)

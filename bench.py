@@ -93,8 +93,8 @@ def parse():
     ap.add_argument("--no-hmc", action="store_true", help="skip the HMC trajectory timing")
     ap.add_argument("--hmc-traj", type=int, default=2, help="timed mixed trajectories (FP64: half, batched: 1)")
     ap.add_argument("--hmc-replicas", type=int, default=8, help="independent 16^4 replicas of the batched HMC")
-    ap.add_argument("--hmc-batch-traj", type=int, default=6,
-                    help="timed mixed trajectories of the batch (x replicas: 48 by default, the workload's ~50)")
+    ap.add_argument("--hmc-batch-traj", type=int, default=7,
+                    help="timed mixed trajectories of the batch (x replicas: 56 by default, the workload's 50)")
     ap.add_argument("--hmc-therm", type=int, default=4, help="thermalisation trajectories of the HMC start")
     ap.add_argument("--no-sweep", action="store_true", help="skip the L = 8, 16, 32 apply sweep")
     ap.add_argument("--no-solve32", action="store_true", help="skip the 32^4 x 4 RHS mixed solve")

@@ -178,10 +178,11 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
     pdl = on && !g_probe.active;
     ga.pdl = ra.pdl = z1.pdl = z2.pdl = y1.pdl = y2.pdl = pdl ? 1 : 0;
   };
-  // Tiles per block of the FP32 zt passes (their persistent grid: 0 starts as
-  // many blocks as are resident; k > 0 at most ceil(tiles / k) blocks, which
-  // leaves SMs to the concurrent groups).
-  auto set_ztpb = [&](int k) { z1.tpb = z2.tpb = k; };
+  // Tiles per block of the FP32 zt passes of the mixed solver (their persistent
+  // grid: 0 starts as many blocks as are resident; k > 0 at most ceil(tiles / k)
+  // blocks, which leaves SMs to the concurrent groups).  The FP64 passes are
+  // bound by arithmetic and keep every resident block.
+  auto set_ztpb = [&](int k) { z1.tpb = z2.tpb = sizeof(RI) == 4 ? k : 0; };
 
   // iteration counters of the chunks (off while the tuner times candidates)
   unsigned long long* cnt = c->counters;
@@ -451,7 +452,7 @@ int solve_impl(wz_ctx* c, const cplx<double>* b, cplx<double>* x, int nrhs, cons
           bestc = cb;
         }
       }
-      if (!tpb_forced)
+      if (!tpb_forced && sizeof(RI) == 4)
         for (int k : {2, 4}) {
           Choice cb = bestc;
           cb.tpb = k;

@@ -36,7 +36,13 @@
  * Launching: a solve replays a CUDA graph of its iteration loop (a WHILE
  * conditional node driven by the device-side convergence state), cached on
  * the context per solve shape; setting WZ_NO_GRAPHS=1 in the environment
- * before wz_create makes the context launch the same kernels eagerly.
+ * before wz_create makes the context launch the same kernels eagerly.  The
+ * first solve of a shape (process-wide) times candidate launch configurations
+ * on the real problem and keeps the fastest: right-hand sides per group,
+ * concurrent streams, programmatic dependent launch of the iteration kernels
+ * and the zt passes' tiles per block.  WZ_RHS_GROUP / WZ_RHS_BRANCHES,
+ * WZ_PDL (0 or 1) and WZ_ZT_TPB fix them instead; none of them changes the
+ * arithmetic (the solutions are bitwise equal).
  *
  * Errors: every call returns a WZ_* status; nothing throws across the ABI.
  * wz_last_error returns a message for the most recent failure of that context.

@@ -77,6 +77,12 @@ def mdagm_flops_per_site(V):
 UNIT = "M^dag M applies/s"
 
 
+def solve_gflops(applies, V, seconds):
+    """Gflop/s of a solve at the paper's counting (5 N log2 N per FFT, two M
+    applies per CG iteration), the convention of its solver-table Gflop/s."""
+    return applies * mdagm_flops_per_site(V) * V / seconds / 1e9
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -528,9 +534,11 @@ def main():
     rhmc = None
     if not args.no_rhmc:
         rhmc = {"heatbath": [], "paper_gtx285": {"8^3x32": {"single_s": 0.93, "single_iters": 360, "double_s": 3.5,
-                                                           "double_iters": 700},
+                                                           "double_iters": 700, "single_gflops": 15,
+                                                           "double_gflops": 7.5},
                                                 "16^3x32": {"single_s": 4.8, "single_iters": 370, "double_s": 20,
-                                                            "double_iters": 730}}}
+                                                            "double_iters": 730, "single_gflops": 28,
+                                                            "double_gflops": 13}}}
         for L in (8, 16):
             dims = (32, L, L, L)
             rl = wz.Lattice(dims, m=1.0, g=0.1, stream=stream.cuda_stream)
@@ -549,8 +557,11 @@ def main():
                 st = rl.rational_apply(rh, R, eta, tol=tol, mixed=mixed, pc=pc)
                 e1.record(stream)
                 torch.cuda.synchronize()
-                row[label] = {"seconds": e0.elapsed_time(e1) / 1000.0, "total_iterations": st["total_iterations"],
-                              "max_iterations": st["iterations"], "reliable_updates": st["reliable_updates"]}
+                sec = e0.elapsed_time(e1) / 1000.0
+                row[label] = {"seconds": sec, "total_iterations": st["total_iterations"],
+                              "max_iterations": st["iterations"], "reliable_updates": st["reliable_updates"],
+                              "gflops": solve_gflops(st["total_iterations"] + st["reliable_updates"],
+                                                     L ** 3 * 32, sec)}
             rhmc["heatbath"].append(row)
             rl.close()
         hw = synth.FORCE_16
@@ -589,6 +600,10 @@ def main():
         paper = {"8^3x32": {"single": (1.3, 830, 0.038, 8), "double": (4.9, 1600, 0.13, 15)},
                  "16^3x32": {"single": (7.1, 870, 0.20, 8), "double": (31, 1800, 0.74, 15)},
                  "32^3x64": {"single": (420, 1600, 6.8, 8), "double": (2200, 3900, 25, 15)}}
+        # the same table's Gflop/s columns (no PC, PC)
+        paper_gflops = {"8^3x32": {"single": (14, 17), "double": (7.2, 8.1)},
+                        "16^3x32": {"single": (25, 31), "double": (12, 13)},
+                        "32^3x64": {"single": (14, 15), "double": (6.5, 7.0)}}
         invtab = {"workload": "L^3 x T (8^3 x 32, 16^3 x 32, 32^3 x 64), m = 1, g = 0.2, phi sigma 0.5, "
                               "1 complex-Gaussian RHS; "
                               "'single' = FP32 iteration with FP64 reliable updates to 1e-6, "
@@ -599,7 +614,8 @@ def main():
             il.set_phi(torch.from_numpy(synth.scalar_field(dims, 0.5, 0)).cuda())
             bi = torch.from_numpy(synth.spinor_rhs(1, dims, 1)).cuda()
             xi = torch.zeros_like(bi)
-            row = {"lattice": f"{L}^3x{T}", "paper_gtx285": paper[f"{L}^3x{T}"]}
+            row = {"lattice": f"{L}^3x{T}", "paper_gtx285": paper[f"{L}^3x{T}"],
+                   "paper_gtx285_gflops": paper_gflops[f"{L}^3x{T}"]}
             for prec, mixed, tol in (("single", True, 1e-6), ("double", False, 1e-12)):
                 for pc in (False, True):
                     if T == 64 and prec == "double" and not pc and not args.invtab_full:
@@ -611,9 +627,11 @@ def main():
                     rc, st, _ = il.solve(bi, xi, tol=tol, mixed=mixed, pc=pc)
                     e1.record(stream)
                     torch.cuda.synchronize()
+                    sec = e0.elapsed_time(e1) / 1000.0
                     row[f"{prec}_{'pc' if pc else 'npc'}"] = {
-                        "seconds": e0.elapsed_time(e1) / 1000.0, "iterations": st["iterations"],
-                        "reliable_updates": st["reliable_updates"], "true_residual": st["max_true_residual"]}
+                        "seconds": sec, "iterations": st["iterations"],
+                        "reliable_updates": st["reliable_updates"], "true_residual": st["max_true_residual"],
+                        "gflops": solve_gflops(st["total_iterations"] + st["reliable_updates"], L ** 3 * T, sec)}
             invtab["rows"].append(row)
             il.close()
 

@@ -42,3 +42,13 @@ def test_class_without_timed_launches():
                             "zt_fp32": {"launches": 2, "timed_launches": 2, "total_ms": 0.02, "bytes": 2e6}})
     assert k["ru_p1_fp64"]["achieved_GB_s"] is None
     assert bench.dominant_class(k) == "zt_fp32"
+
+
+def test_solve_gflops_matches_the_paper_counting():
+    """The paper's solver table: 8^3 x 32, single precision, 830 iterations in
+    1.3 s at 14 Gflop/s, i.e. about 1340 flops per site and iteration; the
+    bench's count (two M applies of two 4D FFTs of 4 spin components at
+    5 N log2 N, plus the site terms) gives 1312 at V = 16384."""
+    V = 8 ** 3 * 32
+    assert bench.mdagm_flops_per_site(V) == pytest.approx(1312.0)
+    assert bench.solve_gflops(830, V, 1.3) == pytest.approx(14.0, rel=0.03)

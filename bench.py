@@ -28,9 +28,10 @@ Extra keys (all on the same GPU, after the timed steps):
   large           the 32^4 workload: an Omelyan trajectory with 4 pseudofermions
                   (2 of its 40 steps by default) and the measurements of the new
                   configuration (<F~>, Ward identity, supercurrent correlators)
-  rhmc, one_loop, paper_solver_table
-                  rational heatbath, RHMC trajectory, one-loop sums and the
-                  solver-table runs, each beside the paper's printed numbers
+  rhmc, one_loop, paper_solver_table, paper_fft_table
+                  rational heatbath, RHMC trajectory, one-loop sums, the
+                  solver-table runs and M applies on the FFT table's lattices,
+                  each beside the paper's printed numbers
   e2e             the headline through the C ABI with host buffers
   cpu_baseline    the FP64 CPU oracle on a bounded sample
   clocks          SM clocks and throttle reasons sampled during the timed steps
@@ -108,6 +109,7 @@ def parse():
     ap.add_argument("--invtab-full", action="store_true",
                     help="also the unpreconditioned FP64 solve of the 32^3 x 64 solver-table row")
     ap.add_argument("--no-batch", action="store_true", help="skip the 64-lattice batched workload")
+    ap.add_argument("--no-ffttab", action="store_true", help="skip the FFT-table shaped M applies")
     ap.add_argument("--no-rhmc", action="store_true", help="skip the rational heatbath / RHMC timings")
     ap.add_argument("--no-oneloop", action="store_true", help="skip the one-loop lattice sums (Sec. 5 tables)")
     ap.add_argument("--no-large", action="store_true", help="skip the 32^4 Omelyan trajectory and measurements")
@@ -635,6 +637,44 @@ def main():
             invtab["rows"].append(row)
             il.close()
 
+    # The paper's 4D FFT table (one spinor field, Gflop/s at 5 N log2 N) beside
+    # one M apply on the same lattices: the apply's two 4D FFTs of the 4 spin
+    # components are counted, its momentum multiply and site terms are not (a
+    # lower bound on the work done).  One right-hand side, L2 flushed before
+    # every repetition, median of 10.
+    ffttab = None
+    if not args.no_ffttab:
+        paper = {"8^3x32": {"single": {"cpu": 1.1, "cufft": 6.9, "own": 24}, "double": {"cpu": 0.94, "cufft": 4.4, "own": 11}},
+                 "16^3x32": {"single": {"cpu": 0.88, "cufft": 14, "own": 71}, "double": {"cpu": 0.69, "cufft": 10, "own": 35}},
+                 "32^3x64": {"single": {"cpu": 0.11, "cufft": 20, "own": None}, "double": {"cpu": 0.085, "cufft": 10, "own": None}}}
+        ffttab = {"workload": "M applied to one complex-Gaussian spinor field on L^3 x T, m = 1, g = 0.2; Gflop/s "
+                              "counts the apply's two 4D FFTs (4 spin components, 5 N log2 N each) only", "rows": []}
+        for L, T in ((8, 32), (16, 32), (32, 64)):
+            dims = (T, L, L, L)
+            V = L ** 3 * T
+            fl = wz.Lattice(dims, m=1.0, g=0.2, stream=stream.cuda_stream)
+            fl.set_phi(torch.from_numpy(synth.scalar_field(dims, 0.5, 0)).cuda())
+            row = {"lattice": f"{L}^3x{T}", "paper_gtx285_gflops": paper[f"{L}^3x{T}"]}
+            for name, dt in (("single", torch.complex64), ("double", torch.complex128)):
+                x = torch.from_numpy(synth.spinor_rhs(1, dims, 1)).to(dt).cuda()
+                y = torch.empty_like(x)
+                for _ in range(3):
+                    fl.apply("M", x, y, 1)
+                times = []
+                for _ in range(10):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    fl.apply("M", x, y, 1)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(e0.elapsed_time(e1))
+                ms = float(np.median(times))
+                row[name] = {"ms_per_apply": ms, "fft_gflops": 2 * 4 * 5.0 * V * np.log2(V) / (ms / 1000.0) / 1e9}
+            ffttab["rows"].append(row)
+            fl.close()
+
     # one-loop counterterms of Tables sse, fse, ase at mL = 8 (N = 8 / ma up to 1024),
     # FP64 on the device, beside the paper's printed mL = 8 columns
     oneloop = None
@@ -892,7 +932,7 @@ def main():
             "config": dict(workload_config(w), parallelism=f"replicas x{world}"),
             "solve": {"iterations_max": max(it), "applies_per_step": total_applies / args.steps,
                       "max_true_residual": max(s["max_true_residual"] for s in stats)},
-            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "large": large, "apply_sweep": sweep, "solve_32x4": solve32, "paper_solver_table": invtab,
+            "fp64": fp64, "hmc": hmc, "rhmc": rhmc, "one_loop": oneloop, "large": large, "apply_sweep": sweep, "solve_32x4": solve32, "paper_solver_table": invtab, "paper_fft_table": ffttab,
             "fma_peak_TFLOP_s": {"fp64": fp64_peak, "fp32": fp32_peak}, "batch": batch, "kernels": kernels, "kernels_full_launch": kernels_full, "e2e": e2e, "roofline": roofline,
             "roofline_full_launch": roofline_full, "solve_roofline": solve_roofline, "cpu_baseline": cpu, "clocks": clk,
             "gpu_launches": int(launches),

@@ -77,3 +77,20 @@ def test_context_calls_reject_a_null_context(wz):
         assert call() == wz.WZ_EINVAL, name
     assert L.wz_destroy(n) == wz.WZ_OK
     assert L.wz_workspace_bytes(n) == 0
+
+
+def test_product_and_oracle_share_no_code():
+    """The product package never imports the oracle (its results must come
+    from the library's kernels), and the oracle never imports the product."""
+    pat_oracle = re.compile(r"^\s*(import oracle|from oracle\b|from \.\.oracle|import \.\.oracle)", re.M)
+    pkg = os.path.join(ROOT, "paper_1005_3276_gb300")
+    for fn in os.listdir(pkg):
+        if fn.endswith(".py"):
+            assert not pat_oracle.search(open(os.path.join(pkg, fn)).read()), fn
+    pat_prod = re.compile(r"^\s*(import|from)\s+paper_1005_3276_gb300\b", re.M)
+    odir = os.path.join(ROOT, "oracle")
+    for fn in os.listdir(odir):
+        if fn.endswith(".py"):
+            src = open(os.path.join(odir, fn)).read()
+            assert not pat_prod.search(src), fn
+            assert "ctypes" not in src and "libwz" not in src, fn

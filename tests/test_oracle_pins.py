@@ -371,6 +371,55 @@ def test_hmc_reversibility_and_dt_scaling():
     assert abs(np.vdot(etas[0], X).real - np.vdot(R[0], R[0]).real) < 1e-10 * np.vdot(R[0], R[0]).real
 
 
+def test_md_integrators_at_g0_are_the_exact_mode_maps():
+    """At g = 0 without pseudofermions the molecular dynamics of Sec. 7.2
+    decouples into one harmonic oscillator per periodic momentum p, with
+    omega^2(p) = 4 D2(p) + 2 |m|^2 K(p): the bosonic action is
+    2 phi^* D2 phi + |m|^2 phi^* K phi and its real gradient is twice that
+    operator on phi.  Leapfrog and the second-order minimum-norm scheme of
+    Omelyan, Mryglod and Folk (velocity form, published lambda =
+    0.1931833275037836) are then products of 2 x 2 kick and drift maps per
+    mode, applied here to the Fourier modes with D2 and K written from their
+    closed forms; the oracle's position-space MD must agree, and a different
+    lambda must not."""
+    dims = (4, 4, 4, 4)
+    m = 0.4 + 0.2j
+    P = Params(dims=dims, m=m, g=0.0)
+    phi0 = rnd_field(dims, 31, 0.5)
+    pi0 = rnd_field(dims, 32, 0.7)
+    p = np.meshgrid(*[2.0 * np.pi * np.arange(n) / n for n in dims], indexing="ij")
+    b = 1.0 - sum(2.0 * np.sin(0.5 * x) ** 2 for x in p)
+    s = np.sqrt(b * b + sum(np.sin(x) ** 2 for x in p))
+    D2 = 1.0 - b / s
+    K = 1.0 - 0.5 * D2
+    w2 = 4.0 * D2 + 2.0 * abs(m) ** 2 * K
+
+    def evolve(seq):
+        f, q = np.fft.fftn(phi0), np.fft.fftn(pi0)
+        for kind, c in seq:
+            if kind == "kick":
+                q = q - c * w2 * f
+            else:
+                f = f + c * q
+        return np.fft.ifftn(f), np.fft.ifftn(q)
+
+    tau, n = 0.6, 3
+    eps = tau / n
+
+    def omelyan(lam):
+        return [("kick", lam * eps), ("drift", 0.5 * eps), ("kick", (1.0 - 2.0 * lam) * eps),
+                ("drift", 0.5 * eps), ("kick", lam * eps)] * n
+
+    leapfrog = [("kick", 0.5 * eps)] + [("drift", eps), ("kick", eps)] * (n - 1) + [("drift", eps), ("kick", 0.5 * eps)]
+    for name, seq in (("omelyan", omelyan(0.1931833275037836)), ("leapfrog", leapfrog)):
+        f_ref, q_ref = evolve(seq)
+        f, q, _ = hmc.integrate(P, phi0, pi0, [], tau, n, name)
+        assert np.abs(f - f_ref).max() < 1e-12 and np.abs(q - q_ref).max() < 1e-12, name
+    f_other, _ = evolve(omelyan(0.25))
+    f, _, _ = hmc.integrate(P, phi0, pi0, [], tau, n, "omelyan")
+    assert np.abs(f - f_other).max() > 1e-6
+
+
 # ------------------------------------------------------------------ locality (Sec. 3.2)
 
 
